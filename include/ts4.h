@@ -1,0 +1,208 @@
+/*
+ * ts4.h -- C ABI of the GB300 (sm_103a) fourth-order Trotter-Suzuki solver for
+ * spin-1/2 dynamics (Dente, Bederian, Zangara, Pastawski, "GPU accelerated
+ * Trotter-Suzuki solver for quantum spin dynamics").
+ *
+ * The library evolves the full 2^N-amplitude state vector of
+ *     H = sum_{i<j} sum_{a=x,y,z} J^a_ij S^a_i S^a_j + sum_i h^a_i S^a_i      (Eq. 1)
+ * with the TS4 step of the XYZ decomposition (Sec. 2):
+ *     U4(tau) = U2(p tau)^2 U2((1-4p) tau) U2(p tau)^2,  p = 1/(4 - 4^{1/3}),
+ *     U2(t)   = U1^dag(-t/2) U1(t/2),  U1(t) = e^{-itH_x} e^{-itH_y} e^{-itH_z},
+ * where e^{-itH_x} = Y e^{-itH~_x} Y^dag and e^{-itH_y} = X e^{-itH~_y} X^dag
+ * map the X and Y parts onto diagonal Z-like phases (Eqs. 5, 7, 9, 10).
+ *
+ * Conventions
+ *   - Spin j (1-based) is bit j-1 of the basis index; bit 1 is spin up
+ *     (S^z = +1/2) (Sec. 3.2: spins are enumerated from right to left).
+ *   - S = sigma/2.  Couplings are N*N row-major float64 matrices; only the
+ *     upper triangle (i < j) is read (each bond once; the diagonal and the lower
+ *     triangle are ignored).  Fields are length-N float64 vectors.
+ *   - The partition order inside U1 is (H_x, H_y, H_z); H_a holds the a-a
+ *     couplings and the a-fields.  The state is in the computational (Z) basis
+ *     before and after every ts_step call.
+ *   - Amplitudes: TS_C64 = interleaved float32 (re, im) pairs (8 bytes per
+ *     amplitude); TS_C128 = interleaved float64 pairs (16 bytes).  2^N of them,
+ *     in basis-index order.
+ *
+ * Threading and streams
+ *   Every call is ordered on the CUDA stream given to ts_create (NULL = the
+ *   legacy default stream).  ts_step and ts_set_basis_state only enqueue work;
+ *   ts_observe, ts_get_state (to host) and ts_set_state (from host) wait for
+ *   their own copies.  A context must not be used from two host threads at once.
+ *
+ * Errors
+ *   Every entry point returns a ts_status; none aborts or throws.  The text of
+ *   the last error of a context is available from ts_last_error.  A CUDA error
+ *   raised by a kernel may surface at a later call (TS_ERR_CUDA).
+ *
+ * Memory ownership
+ *   Inputs passed by pointer are copied; the caller keeps ownership.  Device
+ *   buffers bound with ts_bind_buffers remain owned by the caller (for example
+ *   torch tensors) and must outlive the context; any buffer not bound is
+ *   allocated by the library with cudaMalloc on first use and freed by
+ *   ts_destroy.
+ */
+#ifndef TS4_H
+#define TS4_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TS4_API __attribute__((visibility("default")))
+#else
+#define TS4_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ts_ctx ts_ctx;
+
+typedef enum {
+    TS_OK = 0,
+    TS_ERR_ARG = -1,     /* invalid argument (size, pointer, non-finite tau, ...) */
+    TS_ERR_OOM = -2,     /* device memory exhausted or the state does not fit */
+    TS_ERR_CUDA = -3,    /* a CUDA runtime call or kernel failed */
+    TS_ERR_TIMEOUT = -4, /* a bounded device-side wait gave up (batched mode) */
+    TS_ERR_STATE = -5    /* call out of order (e.g. echo without a saved reference) */
+} ts_status;
+
+typedef enum {
+    TS_C64 = 0,  /* complex64 state, FP32 butterflies; angles formed in FP64 */
+    TS_C128 = 1  /* complex128 state, FP64 throughout */
+} ts_prec;
+
+/* Observables for ts_observe (Sec. 4.2). */
+enum {
+    TS_NORM = 1,   /* sum_s |psi_s|^2                                    -> 1 double */
+    TS_ENERGY = 2, /* <psi|H|psi> = <H_x> + <H_y> + <H_z>                -> 1 double */
+    TS_SZ = 3,     /* <S^z_j> for j = 1..N                               -> N doubles */
+    TS_ECHO = 4,   /* Loschmidt echo |<psi_0|psi>|^2 (Eq. 11, Sigma = 0)
+                      against the reference saved by ts_save_reference   -> 1 double */
+    TS_OVERLAP = 5 /* <psi_0|psi> as (re, im)                            -> 2 doubles */
+};
+
+/* Kernels for the rotation layers (ts_set_schedule). */
+enum {
+    TS_KERNEL_FUSED = 0, /* tiled pass kernel: one HBM round trip per bit group  */
+    TS_KERNEL_BASIC = 1  /* one launch per spin and per phase (the paper's GPU-Basic) */
+};
+
+/*
+ * Creates a context for N spins (1 <= N <= 34).
+ *   Jx, Jy, Jz  N*N row-major couplings J^a_ij (upper triangle read), host memory.
+ *   h           N z-fields h^z_i, host memory, or NULL for no field.
+ *   prec        TS_C64 or TS_C128.
+ *   cuda_stream cudaStream_t to order all work on, or NULL.
+ * Uploads the couplings (FP64) and allocates small device tables.  The state
+ * buffer itself is bound (ts_bind_buffers) or allocated on first use, so a
+ * context can be created before deciding where the 2^N amplitudes live.
+ * Errors: TS_ERR_ARG (N out of range, NULL out/J, non-finite entries),
+ * TS_ERR_CUDA, TS_ERR_OOM.
+ */
+TS4_API ts_status ts_create(ts_ctx **out, int N, const double *Jx, const double *Jy, const double *Jz,
+                    const double *h, ts_prec prec, void *cuda_stream);
+
+/*
+ * Adds transverse fields h^x_i, h^y_i (host, length N; either may be NULL for
+ * zero).  They join H_x and H_y and are rotated with them (Eqs. 6-7).
+ */
+TS4_API ts_status ts_set_transverse_fields(ts_ctx *ctx, const double *hx, const double *hy);
+
+/*
+ * Binds caller-owned device buffers (each of 2^N amplitudes of the context's
+ * precision, 256-byte aligned): psi holds the state; ref (may be NULL) holds
+ * the echo reference; scratch (may be NULL) is used by TS_ENERGY.  Buffers
+ * previously allocated by the library are freed.  Errors: TS_ERR_ARG for a
+ * NULL psi, a size below 2^N amplitudes or a misaligned pointer.
+ */
+TS4_API ts_status ts_bind_buffers(ts_ctx *ctx, void *psi, void *ref, void *scratch, size_t bytes_each);
+
+/* Copies 2^N amplitudes into the state (from host memory if on_device == 0). */
+TS4_API ts_status ts_set_state(ts_ctx *ctx, const void *amps, int on_device);
+
+/* Sets the state to the computational basis state |s> (Eq. 2 with one c_i = 1). */
+TS4_API ts_status ts_set_basis_state(ts_ctx *ctx, uint64_t s);
+
+/* Copies the current state into the echo reference psi_0 (Eq. 11). */
+TS4_API ts_status ts_save_reference(ts_ctx *ctx);
+
+/*
+ * Advances the state by nsteps TS4 steps of length tau: psi <- U4(tau)^nsteps psi
+ * (Sec. 2).  tau < 0 runs backwards (U4(-tau) = U4(tau)^{-1}, used for the
+ * Loschmidt echo of Sec. 4.2).  Asynchronous.  Errors: TS_ERR_ARG (non-finite
+ * tau, nsteps < 0), TS_ERR_OOM, TS_ERR_CUDA.
+ */
+TS4_API ts_status ts_step(ts_ctx *ctx, double tau, int64_t nsteps);
+
+/*
+ * Lower-order variants (Sec. 2): order 1 applies U1(tau), order 2 applies
+ * U2(tau), order 4 is ts_step.  nsteps applications.
+ */
+TS4_API ts_status ts_step_order(ts_ctx *ctx, int order, double tau, int64_t nsteps);
+
+/*
+ * Evaluates an observable (TS_NORM, TS_ENERGY, TS_SZ, TS_ECHO, TS_OVERLAP)
+ * into host memory `out` (sizes above).  Sums are accumulated in FP64.
+ * Synchronises the context's stream.  TS_ECHO/TS_OVERLAP without a saved
+ * reference return TS_ERR_STATE.
+ */
+TS4_API ts_status ts_observe(ts_ctx *ctx, int what, double *out);
+
+/* Copies the state out (to host memory if on_device == 0). */
+TS4_API ts_status ts_get_state(ts_ctx *ctx, void *amps, int on_device);
+
+/* Frees everything the library allocated.  NULL is accepted. */
+TS4_API ts_status ts_destroy(ts_ctx *ctx);
+
+/* Text of the last error of ctx (never NULL; "" if none).  ctx may be NULL. */
+TS4_API const char *ts_last_error(const ts_ctx *ctx);
+
+/*
+ * Selects the rotation kernel and its tile shape (Secs. 3.3-3.4; the paper
+ * searched these by brute force per N, Sec. 3.4 last paragraph).
+ *   kernel          TS_KERNEL_FUSED or TS_KERNEL_BASIC
+ *   tile_bits       log2 of the amplitudes one thread block holds (0 = default)
+ *   coalesce_bits   the s lowest spins every block keeps, so that each block
+ *                   touches runs of 2^s consecutive amplitudes (0 = default)
+ * Errors: TS_ERR_ARG for a shape this build does not provide.
+ */
+TS4_API ts_status ts_set_schedule(ts_ctx *ctx, int kernel, int tile_bits, int coalesce_bits);
+
+/*
+ * Reports the schedule in use: kernel, tile bits, coalescing bits, number of
+ * bit groups g, and HBM passes per TS4 step when chained (20 (g - 1) for the
+ * fused kernel).  Any pointer may be NULL.
+ */
+TS4_API ts_status ts_get_schedule(const ts_ctx *ctx, int *kernel, int *tile_bits, int *coalesce_bits,
+                          int *groups, int *passes_per_step);
+
+/*
+ * The time-step bound of Eq. 4: returns
+ *   [ max_{j,k} ( sum_a (h^a_j/2)^2 + sum_a (J^a_jk/4)^2 )^{1/2} ]^{-1}
+ * for the context's Hamiltonian; steps should satisfy |tau| << this value.
+ */
+TS4_API double ts_step_bound(const ts_ctx *ctx);
+
+/*
+ * Global basis index of local amplitude e of thread block f for a tile made of
+ * the global bits [0, c) and [w, w + h) (Secs. 3.3-3.4: the block index fixes
+ * the other spins).  Local bits [0, h) are the window, local bits [h, h + c)
+ * the c lowest spins.  Host-side copy of the mapping the kernels use; exported
+ * so that it can be checked against the paper's block tables.
+ */
+TS4_API uint64_t ts_tile_global_index(int N, int c, int w, int h, uint64_t f, uint64_t e);
+
+/* Number of CUDA kernels this context has launched so far. */
+TS4_API int64_t ts_kernel_launches(const ts_ctx *ctx);
+
+/* Library version string. */
+TS4_API const char *ts_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TS4_H */

@@ -1,0 +1,1107 @@
+// Host side of the TS4 library: the C ABI of include/ts4.h, the context, the
+// schedule builder (slots and bit-group passes) and the launches.
+//
+// Schedule (Sec. 2 and Secs. 3.3-3.4):
+//   * ts_step expands U4(tau)^n into L = 20 n Walsh-Hadamard layers and L + 1
+//     diagonal slots (see ts4_common.cuh for the slot algebra).
+//   * The fused kernel covers the N spins with g bit groups: G_1 = the TB
+//     lowest spins, then windows of at most TB - s higher spins, each tile also
+//     keeping the s lowest spins so that it reads runs of 2^s consecutive
+//     amplitudes (Sec. 3.4, "coalescing").  A layer is done when every group
+//     has been rotated; the slot that follows is applied inside the pass of the
+//     layer's last group, which then starts the next layer on the same group
+//     (groups are visited in alternating order).  Passes per chained TS4 step:
+//     20 (g - 1).
+#include "../../include/ts4.h"
+#include "ts4_kernels.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+using namespace ts4;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    bool own = false;
+};
+
+struct HostSlot {
+    double t = 0.0, th0 = 0.0, mag = 1.0;
+    int alpha = 2, pcq = 0, scale_exp = 0;
+    Slot dev() const
+    {
+        Slot s;
+        s.t = t;
+        s.th0 = th0;
+        s.mag = mag;
+        s.alpha = alpha;
+        s.pcq = pcq;
+        s.scale_exp = scale_exp;
+        s.pad = 0;
+        return s;
+    }
+};
+
+struct Group {
+    int c, w, h;
+};
+
+struct HostPass {
+    int group = 0;
+    int nsteps = 0;
+    StepDesc steps[kMaxSteps];
+    int slot = -1;      // slot index or -1
+    int phase_k = 0;    // chunk of the step that applies the slot
+    int tab = -1;
+};
+
+struct Schedule {
+    // key
+    int order = 0;
+    double tau = 0.0;
+    int64_t n = -1;
+    int kernel = -1, TB = 0, cbits = 0, slot0_pcq = -1, mode = 0;
+    // content
+    std::vector<HostSlot> slots;
+    std::vector<Group> groups;
+    std::vector<HostPass> passes;
+    std::vector<unsigned char> tabs;    // host image of the PassTab array
+    size_t tab_size = 0;
+};
+
+constexpr int kMaxN = 34;
+
+} // namespace
+
+struct ts_ctx {
+    int N = 0;
+    ts_prec prec = TS_C64;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sms = 0;
+    std::vector<double> Jq;   // [3][N][N] symmetric, J/4
+    std::vector<double> hh;   // [3][N], h/2
+    std::vector<double> Jraw[3];
+    std::vector<double> hraw[3];
+    double *dJq = nullptr, *dhh = nullptr;
+    Buf psi, ref, scratch;
+    bool ref_valid = false;
+    double *dpart = nullptr;
+    size_t part_cap = 0;      // doubles
+    double *hout = nullptr;   // pinned, kMaxN + 8 doubles
+    void *dtab = nullptr;
+    size_t tab_cap = 0;
+    int kernel = TS_KERNEL_FUSED;
+    int TB = 0, RB = 0, cbits = 0;
+    Schedule sched;       // last ts_step schedule
+    Schedule sched_obs;   // frame rotation used by TS_ENERGY
+    std::string err;
+    int64_t launches = 0;
+};
+
+namespace {
+
+ts_status fail(ts_ctx *ctx, ts_status st, const std::string &msg)
+{
+    if (ctx)
+        ctx->err = msg;
+    return st;
+}
+
+ts_status cuda_fail(ts_ctx *ctx, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? TS_ERR_OOM : TS_ERR_CUDA, m);
+}
+
+#define TS_CUDA(ctx, call)                                                                        \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return cuda_fail((ctx), e_, #call);                                                   \
+    } while (0)
+
+size_t amp_bytes(const ts_ctx *ctx) { return ctx->prec == TS_C64 ? 8 : 16; }
+uint64_t dim_of(const ts_ctx *ctx) { return UINT64_C(1) << ctx->N; }
+size_t state_bytes(const ts_ctx *ctx) { return (size_t)dim_of(ctx) * amp_bytes(ctx); }
+
+// ------------------------------------------------------------ kernel shapes
+
+// Register bits per precision and the tile sizes this build provides.
+int reg_bits(ts_prec p) { return p == TS_C64 ? 5 : 4; }
+bool tile_supported(ts_prec p, int tb)
+{
+    return p == TS_C64 ? (tb >= 11 && tb <= 14) : (tb >= 10 && tb <= 13);
+}
+int default_tile(ts_prec p) { return p == TS_C64 ? 14 : 12; }
+int default_cbits(ts_prec p) { return p == TS_C64 ? 3 : 2; }
+
+template <typename R, int TB, int RB>
+cudaError_t launch_pass_t(cudaStream_t st, void *psi, const PassArgs &a, const void *tabs, uint64_t nblk)
+{
+    constexpr int NT = 1 << (TB - RB);
+    constexpr size_t smem = sizeof(typename CT<R>::T) << TB;
+    cudaError_t e = cudaFuncSetAttribute(k_pass<R, TB, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    k_pass<R, TB, RB><<<(unsigned)nblk, NT, smem, st>>>((typename CT<R>::T *)psi, a,
+                                                         (const PassTab<R, TB, RB> *)tabs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass(const ts_ctx *ctx, void *psi, const PassArgs &a, const void *tabs, uint64_t nblk)
+{
+    if (ctx->prec == TS_C64) {
+        switch (ctx->TB) {
+        case 11: return launch_pass_t<float, 11, 5>(ctx->stream, psi, a, tabs, nblk);
+        case 12: return launch_pass_t<float, 12, 5>(ctx->stream, psi, a, tabs, nblk);
+        case 13: return launch_pass_t<float, 13, 5>(ctx->stream, psi, a, tabs, nblk);
+        default: return launch_pass_t<float, 14, 5>(ctx->stream, psi, a, tabs, nblk);
+        }
+    }
+    switch (ctx->TB) {
+    case 10: return launch_pass_t<double, 10, 4>(ctx->stream, psi, a, tabs, nblk);
+    case 11: return launch_pass_t<double, 11, 4>(ctx->stream, psi, a, tabs, nblk);
+    case 12: return launch_pass_t<double, 12, 4>(ctx->stream, psi, a, tabs, nblk);
+    default: return launch_pass_t<double, 13, 4>(ctx->stream, psi, a, tabs, nblk);
+    }
+}
+
+template <typename R, int TB, int RB> size_t tab_size_t() { return sizeof(PassTab<R, TB, RB>); }
+
+size_t tab_size(ts_prec p, int TB)
+{
+    if (p == TS_C64) {
+        switch (TB) {
+        case 11: return tab_size_t<float, 11, 5>();
+        case 12: return tab_size_t<float, 12, 5>();
+        case 13: return tab_size_t<float, 13, 5>();
+        default: return tab_size_t<float, 14, 5>();
+        }
+    }
+    switch (TB) {
+    case 10: return tab_size_t<double, 10, 4>();
+    case 11: return tab_size_t<double, 11, 4>();
+    case 12: return tab_size_t<double, 12, 4>();
+    default: return tab_size_t<double, 13, 4>();
+    }
+}
+
+// Host FP64 construction of one PassTab (A over the tile's local bits, QK for the slot's chunk).
+template <typename R, int TB, int RB>
+void build_tab_t(unsigned char *dst, const ts_ctx *ctx, const HostSlot &sl, const Group &g, int phase_k)
+{
+    using C = typename CT<R>::T;
+    PassTab<R, TB, RB> tb;
+    std::memset(&tb, 0, sizeof(tb));
+    const int N = ctx->N;
+    const double *Jq = ctx->Jq.data() + (size_t)sl.alpha * N * N;
+    auto pos = [&](int l) { return l < g.h ? g.w + l : l - g.h; };
+    std::vector<double> A(TB * TB, 0.0);
+    for (int l = 0; l < TB; l++)
+        for (int m = 0; m < TB; m++)
+            if (l != m)
+                A[l * TB + m] = sl.t * Jq[pos(l) * N + pos(m)];
+    for (int k = 0; k < TB * TB; k++)
+        tb.A[k] = (R)(A[k] / M_PI);
+    const int W = (phase_k * RB < TB - RB) ? phase_k * RB : TB - RB;
+    for (int j = 0; j < (1 << RB); j++) {
+        double q = 0.0;
+        for (int l = 0; l < RB; l++)
+            for (int m = l + 1; m < RB; m++) {
+                const double sl_ = ((j >> l) & 1) ? 1.0 : -1.0;
+                const double sm_ = ((j >> m) & 1) ? 1.0 : -1.0;
+                q += A[(W + l) * TB + (W + m)] * sl_ * sm_;
+            }
+        double re = std::cos(q), im = -std::sin(q);
+        const int k = (sl.pcq * __builtin_popcount((unsigned)j)) & 3;
+        for (int r = 0; r < k; r++) { // multiply by i
+            double t = re;
+            re = -im;
+            im = t;
+        }
+        C z;
+        z.x = (R)re;
+        z.y = (R)im;
+        tb.QK[j] = z;
+    }
+    std::memcpy(dst, &tb, sizeof(tb));
+}
+
+void build_tab(unsigned char *dst, const ts_ctx *ctx, const HostSlot &sl, const Group &g, int phase_k)
+{
+    if (ctx->prec == TS_C64) {
+        switch (ctx->TB) {
+        case 11: return build_tab_t<float, 11, 5>(dst, ctx, sl, g, phase_k);
+        case 12: return build_tab_t<float, 12, 5>(dst, ctx, sl, g, phase_k);
+        case 13: return build_tab_t<float, 13, 5>(dst, ctx, sl, g, phase_k);
+        default: return build_tab_t<float, 14, 5>(dst, ctx, sl, g, phase_k);
+        }
+    }
+    switch (ctx->TB) {
+    case 10: return build_tab_t<double, 10, 4>(dst, ctx, sl, g, phase_k);
+    case 11: return build_tab_t<double, 11, 4>(dst, ctx, sl, g, phase_k);
+    case 12: return build_tab_t<double, 12, 4>(dst, ctx, sl, g, phase_k);
+    default: return build_tab_t<double, 13, 4>(dst, ctx, sl, g, phase_k);
+    }
+}
+
+// ------------------------------------------------------------ slots (Sec. 2)
+
+int half_scale(int N, int k) { return (k & 1) ? N / 2 : N - N / 2; }
+
+// Slots of U4(tau)^n (order 4), U2(tau)^n (order 2) or U1(tau)^n (order 1).
+std::vector<HostSlot> make_slots(int N, int order, double tau, int64_t n)
+{
+    std::vector<HostSlot> s;
+    HostSlot z;
+    if (order == 4 || order == 2) {
+        const double p = 1.0 / (4.0 - std::cbrt(4.0));
+        const double c4[5] = {p, p, 1.0 - 4.0 * p, p, p};
+        const int per = (order == 4) ? 5 : 1;
+        const int64_t U = n * per;
+        auto tu = [&](int64_t u) { return (order == 4 ? c4[u % 5] : 1.0) * tau; };
+        s.reserve((size_t)(4 * U + 1));
+        z.t = tu(0) / 2;
+        z.alpha = 2;
+        z.pcq = 3;
+        s.push_back(z);
+        for (int64_t u = 0; u < U; u++) {
+            const double t = tu(u);
+            const int64_t k = 4 * u;
+            HostSlot a;
+            a.t = t / 2; a.alpha = 1; a.pcq = 1; a.scale_exp = half_scale(N, (int)((k + 1) & 1));
+            s.push_back(a);
+            HostSlot b;
+            b.t = t; b.alpha = 0; b.pcq = 0; b.scale_exp = half_scale(N, (int)((k + 2) & 1));
+            s.push_back(b);
+            HostSlot c;
+            c.t = t / 2; c.alpha = 1; c.pcq = 3; c.scale_exp = half_scale(N, (int)((k + 3) & 1));
+            s.push_back(c);
+            HostSlot d;
+            d.alpha = 2;
+            d.scale_exp = half_scale(N, (int)((k + 4) & 1));
+            if (u + 1 < U) {
+                d.t = (t + tu(u + 1)) / 2;
+                d.pcq = 0;
+            } else {
+                d.t = t / 2;
+                d.pcq = 1;
+            }
+            s.push_back(d);
+        }
+    } else {
+        // U1(tau) = e^{-i tau H_x} e^{-i tau H_y} e^{-i tau H_z}: layers X^dag, Y^dag X, Y
+        z.t = tau;
+        z.alpha = 2;
+        z.pcq = 3;
+        s.push_back(z);
+        for (int64_t u = 0; u < n; u++) {
+            const int64_t k = 3 * u;
+            HostSlot a;
+            a.t = tau; a.alpha = 1; a.pcq = 1; a.scale_exp = half_scale(N, (int)((k + 1) & 1));
+            s.push_back(a);
+            HostSlot b;
+            b.t = tau; b.alpha = 0; b.pcq = 1; b.th0 = M_PI * N / 4.0;
+            b.scale_exp = half_scale(N, (int)((k + 2) & 1));
+            s.push_back(b);
+            HostSlot c;
+            c.alpha = 2;
+            c.scale_exp = half_scale(N, (int)((k + 3) & 1));
+            if (u + 1 < n) {
+                c.t = tau;
+                c.pcq = 1;
+            } else {
+                c.t = 0.0;
+                c.pcq = 2;
+            }
+            s.push_back(c);
+        }
+    }
+    // with N * layers odd the powers of two fall short by sqrt 2: fold it into the last slot
+    const int64_t L = (int64_t)s.size() - 1;
+    if ((N & 1) && (L & 1))
+        s.back().mag = std::sqrt(0.5);
+    return s;
+}
+
+// ------------------------------------------------------------ groups and passes
+
+std::vector<Group> make_groups(int N, int TB, int cbits)
+{
+    std::vector<Group> g;
+    if (N <= TB) {
+        g.push_back({0, 0, N});
+        return g;
+    }
+    g.push_back({0, 0, TB});
+    const int rest = N - TB;
+    const int hmax = TB - cbits;
+    const int ng = (rest + hmax - 1) / hmax;
+    const int base = rest / ng, extra = rest % ng;
+    int w = TB;
+    for (int k = 0; k < ng; k++) {
+        const int hk = base + (k < extra ? 1 : 0);
+        g.push_back({TB - hk, w, hk});
+        w += hk;
+    }
+    return g;
+}
+
+struct ChunkInfo {
+    int n;
+    int lo[8], hi[8];
+};
+
+ChunkInfo chunks_of(int h, int TB, int RB)
+{
+    ChunkInfo ci;
+    ci.n = (h + RB - 1) / RB;
+    for (int k = 0; k < ci.n; k++) {
+        const int W = (k * RB < TB - RB) ? k * RB : TB - RB;
+        ci.lo[k] = k * RB - W;
+        ci.hi[k] = ((k + 1) * RB < h ? (k + 1) * RB : h) - W;
+    }
+    return ci;
+}
+
+enum PassKind { P_PHASE_ROT, P_ROT, P_ROT_PHASE_ROT, P_ROT_PHASE, P_PHASE };
+
+HostPass make_pass(int gi, const Group &g, PassKind kind, int slot, int TB, int RB)
+{
+    HostPass p;
+    p.group = gi;
+    p.slot = slot;
+    ChunkInfo ci = chunks_of(g.h, TB, RB);
+    auto add = [&](int k, bool r0, bool ph, bool r1) {
+        StepDesc d;
+        std::memset(&d, 0, sizeof(d));
+        d.k = (uint8_t)k;
+        d.r0lo = (uint8_t)(r0 ? ci.lo[k] : 0);
+        d.r0hi = (uint8_t)(r0 ? ci.hi[k] : 0);
+        d.ph = ph ? 1 : 0;
+        d.r1lo = (uint8_t)(r1 ? ci.lo[k] : 0);
+        d.r1hi = (uint8_t)(r1 ? ci.hi[k] : 0);
+        if (ph)
+            p.phase_k = k;
+        p.steps[p.nsteps++] = d;
+    };
+    const int n = ci.n;
+    switch (kind) {
+    case P_PHASE_ROT:
+        add(0, false, true, true);
+        for (int k = 1; k < n; k++)
+            add(k, true, false, false);
+        break;
+    case P_ROT:
+        for (int k = 0; k < n; k++)
+            add(k, true, false, false);
+        break;
+    case P_ROT_PHASE_ROT:
+        for (int k = 0; k < n - 1; k++)
+            add(k, true, false, false);
+        add(n - 1, true, true, true);
+        for (int k = n - 2; k >= 0; k--)
+            add(k, true, false, false);
+        break;
+    case P_ROT_PHASE:
+        for (int k = 0; k < n - 1; k++)
+            add(k, true, false, false);
+        add(n - 1, true, true, false);
+        break;
+    case P_PHASE:
+        add(0, false, true, false);
+        break;
+    }
+    return p;
+}
+
+// Passes for L layers and slots 0..L (slot 0 before the first layer).
+std::vector<HostPass> make_passes(const std::vector<Group> &G, int64_t L, int TB, int RB)
+{
+    std::vector<HostPass> P;
+    const int g = (int)G.size();
+    if (g == 1) {
+        P.reserve((size_t)L + 1);
+        for (int64_t l = 0; l < L; l++)
+            P.push_back(make_pass(0, G[0], P_PHASE_ROT, (int)l, TB, RB));
+        P.push_back(make_pass(0, G[0], P_PHASE, (int)L, TB, RB));
+        return P;
+    }
+    P.reserve((size_t)(1 + L * (g - 1)));
+    P.push_back(make_pass(0, G[0], P_PHASE_ROT, 0, TB, RB));
+    for (int64_t l = 1; l <= L; l++) {
+        // layer l visits the groups forward when l is odd, backward when even
+        std::vector<int> ord(g);
+        for (int k = 0; k < g; k++)
+            ord[k] = (l & 1) ? k : g - 1 - k;
+        for (int k = 1; k < g - 1; k++)
+            P.push_back(make_pass(ord[k], G[ord[k]], P_ROT, -1, TB, RB));
+        const int last = ord[g - 1];
+        if (l < L)
+            P.push_back(make_pass(last, G[last], P_ROT_PHASE_ROT, (int)l, TB, RB));
+        else
+            P.push_back(make_pass(last, G[last], P_ROT_PHASE, (int)l, TB, RB));
+    }
+    return P;
+}
+
+// ------------------------------------------------------------ buffers
+
+ts_status ensure_buf(ts_ctx *ctx, Buf &b, const char *what)
+{
+    if (b.p)
+        return TS_OK;
+    size_t freeb = 0, totb = 0;
+    TS_CUDA(ctx, cudaMemGetInfo(&freeb, &totb));
+    if (state_bytes(ctx) > freeb)
+        return fail(ctx, TS_ERR_OOM, std::string(what) + ": state of " + std::to_string(state_bytes(ctx)) +
+                                         " bytes does not fit in free device memory");
+    cudaError_t e = cudaMalloc(&b.p, state_bytes(ctx));
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return cuda_fail(ctx, e, what);
+    }
+    b.own = true;
+    return TS_OK;
+}
+
+void free_buf(Buf &b)
+{
+    if (b.p && b.own)
+        cudaFree(b.p);
+    b.p = nullptr;
+    b.own = false;
+}
+
+ts_status ensure_part(ts_ctx *ctx, size_t doubles)
+{
+    if (ctx->part_cap >= doubles)
+        return TS_OK;
+    if (ctx->dpart)
+        cudaFree(ctx->dpart);
+    ctx->dpart = nullptr;
+    TS_CUDA(ctx, cudaMalloc(&ctx->dpart, doubles * sizeof(double)));
+    ctx->part_cap = doubles;
+    return TS_OK;
+}
+
+// ------------------------------------------------------------ execution
+
+HamDev ham_dev(const ts_ctx *ctx)
+{
+    HamDev h;
+    h.Jq = ctx->dJq;
+    h.hh = ctx->dhh;
+    h.N = ctx->N;
+    return h;
+}
+
+unsigned grid_for(const ts_ctx *ctx, uint64_t work, int threads)
+{
+    uint64_t blocks = (work + threads - 1) / threads;
+    const uint64_t cap = (uint64_t)ctx->sms * 16;
+    if (blocks > cap)
+        blocks = cap;
+    return (unsigned)(blocks ? blocks : 1);
+}
+
+ts_status run_basic(ts_ctx *ctx, void *buf, const std::vector<HostSlot> &slots)
+{
+    const uint64_t dim = dim_of(ctx);
+    const unsigned gs = grid_for(ctx, dim, 256), gp = grid_for(ctx, dim / 2, 256);
+    const HamDev hd = ham_dev(ctx);
+    for (size_t k = 0; k < slots.size(); k++) {
+        if (k > 0) {
+            for (int b = 0; b < ctx->N; b++) {
+                if (ctx->prec == TS_C64)
+                    k_wht_bit<float2><<<gp, 256, 0, ctx->stream>>>((float2 *)buf, dim / 2, b);
+                else
+                    k_wht_bit<double2><<<gp, 256, 0, ctx->stream>>>((double2 *)buf, dim / 2, b);
+                ctx->launches++;
+            }
+        }
+        const Slot sl = slots[k].dev();
+        if (ctx->prec == TS_C64)
+            k_slot_basic<float><<<gs, 256, 0, ctx->stream>>>((float2 *)buf, dim, hd, sl);
+        else
+            k_slot_basic<double><<<gs, 256, 0, ctx->stream>>>((double2 *)buf, dim, hd, sl);
+        ctx->launches++;
+        TS_CUDA(ctx, cudaGetLastError());
+    }
+    return TS_OK;
+}
+
+// Builds (or reuses) the fused schedule for the given slots.
+ts_status prepare_fused(ts_ctx *ctx, Schedule &S)
+{
+    const int RB = ctx->RB;
+    S.groups = make_groups(ctx->N, ctx->TB, ctx->cbits);
+    const int64_t L = (int64_t)S.slots.size() - 1;
+    S.passes = make_passes(S.groups, L, ctx->TB, RB);
+    // one table per distinct (slot values, group, phase chunk)
+    S.tab_size = tab_size(ctx->prec, ctx->TB);
+    std::map<std::tuple<double, int, int, int, int>, int> seen;
+    S.tabs.clear();
+    for (auto &p : S.passes) {
+        if (p.slot < 0)
+            continue;
+        const HostSlot &sl = S.slots[p.slot];
+        auto key = std::make_tuple(sl.t, sl.alpha, sl.pcq, p.group, p.phase_k);
+        auto it = seen.find(key);
+        if (it != seen.end()) {
+            p.tab = it->second;
+            continue;
+        }
+        const int idx = (int)seen.size();
+        seen[key] = idx;
+        p.tab = idx;
+        S.tabs.resize((size_t)(idx + 1) * S.tab_size);
+        build_tab(S.tabs.data() + (size_t)idx * S.tab_size, ctx, sl, S.groups[p.group], p.phase_k);
+    }
+    if (S.tabs.size() > ctx->tab_cap) {
+        if (ctx->dtab)
+            cudaFree(ctx->dtab);
+        ctx->dtab = nullptr;
+        ctx->tab_cap = 0;
+        TS_CUDA(ctx, cudaMalloc(&ctx->dtab, S.tabs.size()));
+        ctx->tab_cap = S.tabs.size();
+    }
+    if (!S.tabs.empty())
+        TS_CUDA(ctx, cudaMemcpyAsync(ctx->dtab, S.tabs.data(), S.tabs.size(), cudaMemcpyHostToDevice, ctx->stream));
+    // the host image must stay valid until the copy is done
+    TS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return TS_OK;
+}
+
+ts_status run_fused(ts_ctx *ctx, void *buf, const Schedule &S)
+{
+    const HamDev hd = ham_dev(ctx);
+    for (const auto &p : S.passes) {
+        const Group &g = S.groups[p.group];
+        PassArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.c = g.c;
+        a.w = g.w;
+        a.h = g.h;
+        a.nsteps = p.nsteps;
+        std::memcpy(a.steps, p.steps, sizeof(p.steps));
+        a.has_slot = p.slot >= 0;
+        if (p.slot >= 0)
+            a.slot = S.slots[p.slot].dev();
+        a.tab = p.tab < 0 ? 0 : p.tab;
+        a.ham = hd;
+        const uint64_t nblk = UINT64_C(1) << (ctx->N - (g.c + g.h));
+        cudaError_t e = launch_pass(ctx, buf, a, ctx->dtab, nblk);
+        ctx->launches++;
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "fused pass launch");
+    }
+    return TS_OK;
+}
+
+bool fused_usable(const ts_ctx *ctx) { return ctx->kernel == TS_KERNEL_FUSED && ctx->N >= ctx->TB; }
+
+// Runs the layers of `slots` on buf with the selected kernel.  The schedule is
+// cached under `key` so that repeated calls reuse the pass list and tables.
+ts_status run_slots(ts_ctx *ctx, Schedule &S, void *buf, int order, double tau, int64_t n, int mode,
+                    const std::vector<HostSlot> &slots)
+{
+    // small N: the fused kernel needs a full tile; take the largest provided tile <= N
+    const int keepTB = ctx->TB;
+    if (ctx->kernel == TS_KERNEL_FUSED && ctx->N < ctx->TB && tile_supported(ctx->prec, ctx->N))
+        ctx->TB = ctx->N;
+    ts_status st = TS_OK;
+    if (!fused_usable(ctx)) {
+        st = run_basic(ctx, buf, slots);
+    } else {
+        const bool hit = S.order == order && S.tau == tau && S.n == n && S.kernel == ctx->kernel &&
+                         S.TB == ctx->TB && S.cbits == ctx->cbits && S.mode == mode;
+        if (!hit) {
+            S = Schedule();
+            S.slots = slots;
+            st = prepare_fused(ctx, S);
+            if (st == TS_OK) {
+                S.order = order;
+                S.tau = tau;
+                S.n = n;
+                S.kernel = ctx->kernel;
+                S.TB = ctx->TB;
+                S.cbits = ctx->cbits;
+                S.mode = mode;
+            } else {
+                S = Schedule();
+            }
+        }
+        if (st == TS_OK)
+            st = run_fused(ctx, buf, S);
+    }
+    ctx->TB = keepTB;
+    return st;
+}
+
+// ------------------------------------------------------------ reductions
+
+ts_status finish_sum(ts_ctx *ctx, int nblk, int K, double *out)
+{
+    // partial sums live in dpart[0 .. nblk*K); the final sums go after them
+    double *dfin = ctx->dpart + (size_t)nblk * K;
+    k_sum_final<<<1, 64, 0, ctx->stream>>>(ctx->dpart, nblk, K, dfin);
+    ctx->launches++;
+    TS_CUDA(ctx, cudaGetLastError());
+    TS_CUDA(ctx, cudaMemcpyAsync(ctx->hout, dfin, K * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    TS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::memcpy(out, ctx->hout, K * sizeof(double));
+    return TS_OK;
+}
+
+unsigned red_blocks(const ts_ctx *ctx, uint64_t work_per_block)
+{
+    uint64_t b = (dim_of(ctx) + work_per_block - 1) / work_per_block;
+    const uint64_t cap = (uint64_t)ctx->sms * 4;
+    if (b > cap)
+        b = cap;
+    return (unsigned)(b ? b : 1);
+}
+
+ts_status sum_sz(ts_ctx *ctx, const void *buf, double *norm_and_p /* N+1 */)
+{
+    const int K = ctx->N + 1;
+    const unsigned nb = red_blocks(ctx, 256 * 32);
+    ts_status st = ensure_part(ctx, (size_t)nb * K + K);
+    if (st)
+        return st;
+    if (ctx->prec == TS_C64)
+        k_sum_sz<float2><<<nb, 256, 0, ctx->stream>>>((const float2 *)buf, ctx->N, ctx->dpart);
+    else
+        k_sum_sz<double2><<<nb, 256, 0, ctx->stream>>>((const double2 *)buf, ctx->N, ctx->dpart);
+    ctx->launches++;
+    TS_CUDA(ctx, cudaGetLastError());
+    return finish_sum(ctx, (int)nb, K, norm_and_p);
+}
+
+ts_status sum_diag(ts_ctx *ctx, const void *buf, int alpha, double *out)
+{
+    const unsigned nb = red_blocks(ctx, 256 * 8);
+    ts_status st = ensure_part(ctx, (size_t)nb + 1);
+    if (st)
+        return st;
+    if (ctx->prec == TS_C64)
+        k_sum_diag_energy<float2><<<nb, 256, 0, ctx->stream>>>((const float2 *)buf, dim_of(ctx), ham_dev(ctx), alpha,
+                                                               ctx->dpart);
+    else
+        k_sum_diag_energy<double2><<<nb, 256, 0, ctx->stream>>>((const double2 *)buf, dim_of(ctx), ham_dev(ctx),
+                                                                alpha, ctx->dpart);
+    ctx->launches++;
+    TS_CUDA(ctx, cudaGetLastError());
+    return finish_sum(ctx, (int)nb, 1, out);
+}
+
+ts_status sum_overlap(ts_ctx *ctx, const void *a, const void *b, double *out2)
+{
+    const unsigned nb = red_blocks(ctx, 256 * 8);
+    ts_status st = ensure_part(ctx, (size_t)nb * 2 + 2);
+    if (st)
+        return st;
+    if (ctx->prec == TS_C64)
+        k_sum_overlap<float2><<<nb, 256, 0, ctx->stream>>>((const float2 *)a, (const float2 *)b, dim_of(ctx),
+                                                           ctx->dpart);
+    else
+        k_sum_overlap<double2><<<nb, 256, 0, ctx->stream>>>((const double2 *)a, (const double2 *)b, dim_of(ctx),
+                                                            ctx->dpart);
+    ctx->launches++;
+    TS_CUDA(ctx, cudaGetLastError());
+    return finish_sum(ctx, (int)nb, 2, out2);
+}
+
+// <H_a> for a = x (pcq 2: Y^dag = 2^{-N/2} W (-1)^pc) or y (pcq 3: X^dag = 2^{-N/2} D W (-i)^pc):
+// one Walsh-Hadamard layer on a copy, then sum |phi_s|^2 E_a(s) 2^{-N}.
+ts_status rotated_energy(ts_ctx *ctx, int alpha, double *out)
+{
+    ts_status st = ensure_buf(ctx, ctx->scratch, "energy scratch buffer");
+    if (st)
+        return st;
+    TS_CUDA(ctx, cudaMemcpyAsync(ctx->scratch.p, ctx->psi.p, state_bytes(ctx), cudaMemcpyDeviceToDevice, ctx->stream));
+    std::vector<HostSlot> sl(2);
+    sl[0].t = 0.0;
+    sl[0].pcq = alpha == 0 ? 2 : 3;
+    sl[1].t = 0.0;
+    st = run_slots(ctx, ctx->sched_obs, ctx->scratch.p, 0, 0.0, 1, 10 + alpha, sl);
+    if (st)
+        return st;
+    double v = 0.0;
+    st = sum_diag(ctx, ctx->scratch.p, alpha, &v);
+    if (st)
+        return st;
+    *out = std::ldexp(v, -ctx->N);
+    return TS_OK;
+}
+
+bool finite_all(const double *p, size_t n)
+{
+    for (size_t i = 0; i < n; i++)
+        if (!std::isfinite(p[i]))
+            return false;
+    return true;
+}
+
+} // namespace
+
+// ================================================================== C ABI
+
+extern "C" {
+
+const char *ts_version(void) { return "ts4-gb300 0.1 (sm_103a)"; }
+
+const char *ts_last_error(const ts_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int64_t ts_kernel_launches(const ts_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+uint64_t ts_tile_global_index(int N, int c, int w, int h, uint64_t f, uint64_t e)
+{
+    (void)N;
+    return tile_global_index(c, w, h, f, e);
+}
+
+ts_status ts_create(ts_ctx **out, int N, const double *Jx, const double *Jy, const double *Jz, const double *h,
+                    ts_prec prec, void *cuda_stream)
+{
+    if (!out)
+        return TS_ERR_ARG;
+    *out = nullptr;
+    if (N < 1 || N > kMaxN || !Jx || !Jy || !Jz || (prec != TS_C64 && prec != TS_C128))
+        return TS_ERR_ARG;
+    const double *J[3] = {Jx, Jy, Jz};
+    for (int a = 0; a < 3; a++)
+        if (!finite_all(J[a], (size_t)N * N))
+            return TS_ERR_ARG;
+    if (h && !finite_all(h, (size_t)N))
+        return TS_ERR_ARG;
+    ts_ctx *ctx = new (std::nothrow) ts_ctx();
+    if (!ctx)
+        return TS_ERR_OOM;
+    ctx->N = N;
+    ctx->prec = prec;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->Jq.assign((size_t)3 * N * N, 0.0);
+    ctx->hh.assign((size_t)3 * N, 0.0);
+    for (int a = 0; a < 3; a++) {
+        ctx->Jraw[a].assign(J[a], J[a] + (size_t)N * N);
+        ctx->hraw[a].assign((size_t)N, 0.0);
+        for (int i = 0; i < N; i++)
+            for (int j = i + 1; j < N; j++) {
+                const double v = J[a][i * N + j] / 4.0;
+                ctx->Jq[(size_t)a * N * N + i * N + j] = v;
+                ctx->Jq[(size_t)a * N * N + j * N + i] = v;
+            }
+    }
+    if (h)
+        for (int i = 0; i < N; i++) {
+            ctx->hraw[2][i] = h[i];
+            ctx->hh[2 * N + i] = h[i] / 2.0;
+        }
+    ctx->RB = reg_bits(prec);
+    ctx->TB = default_tile(prec);
+    ctx->cbits = default_cbits(prec);
+    ts_status st = TS_OK;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&ctx->dJq, ctx->Jq.size() * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&ctx->dhh, ctx->hh.size() * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->dJq, ctx->Jq.data(), ctx->Jq.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->dhh, ctx->hh.data(), ctx->hh.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMallocHost(&ctx->hout, (kMaxN + 8) * sizeof(double));
+    if (e != cudaSuccess) {
+        st = (e == cudaErrorMemoryAllocation) ? TS_ERR_OOM : TS_ERR_CUDA;
+        ts_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return TS_OK;
+}
+
+ts_status ts_set_transverse_fields(ts_ctx *ctx, const double *hx, const double *hy)
+{
+    if (!ctx)
+        return TS_ERR_ARG;
+    const int N = ctx->N;
+    if ((hx && !finite_all(hx, N)) || (hy && !finite_all(hy, N)))
+        return fail(ctx, TS_ERR_ARG, "ts_set_transverse_fields: non-finite field");
+    for (int i = 0; i < N; i++) {
+        ctx->hraw[0][i] = hx ? hx[i] : 0.0;
+        ctx->hraw[1][i] = hy ? hy[i] : 0.0;
+        ctx->hh[0 * N + i] = hx ? hx[i] / 2.0 : 0.0;
+        ctx->hh[1 * N + i] = hy ? hy[i] / 2.0 : 0.0;
+    }
+    TS_CUDA(ctx, cudaMemcpyAsync(ctx->dhh, ctx->hh.data(), ctx->hh.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    TS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->sched = Schedule();
+    ctx->sched_obs = Schedule();
+    return TS_OK;
+}
+
+ts_status ts_bind_buffers(ts_ctx *ctx, void *psi, void *ref, void *scratch, size_t bytes_each)
+{
+    if (!ctx)
+        return TS_ERR_ARG;
+    if (!psi)
+        return fail(ctx, TS_ERR_ARG, "ts_bind_buffers: psi is NULL");
+    if (bytes_each < state_bytes(ctx))
+        return fail(ctx, TS_ERR_ARG, "ts_bind_buffers: buffers hold fewer than 2^N amplitudes");
+    for (void *p : {psi, ref, scratch})
+        if (p && ((uintptr_t)p & 255))
+            return fail(ctx, TS_ERR_ARG, "ts_bind_buffers: buffer not 256-byte aligned");
+    free_buf(ctx->psi);
+    ctx->psi.p = psi;
+    if (ref) {
+        free_buf(ctx->ref);
+        ctx->ref.p = ref;
+        ctx->ref_valid = false;
+    }
+    if (scratch) {
+        free_buf(ctx->scratch);
+        ctx->scratch.p = scratch;
+    }
+    return TS_OK;
+}
+
+ts_status ts_set_state(ts_ctx *ctx, const void *amps, int on_device)
+{
+    if (!ctx || !amps)
+        return ctx ? fail(ctx, TS_ERR_ARG, "ts_set_state: NULL amplitudes") : TS_ERR_ARG;
+    ts_status st = ensure_buf(ctx, ctx->psi, "state buffer");
+    if (st)
+        return st;
+    TS_CUDA(ctx, cudaMemcpyAsync(ctx->psi.p, amps, state_bytes(ctx),
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    if (!on_device)
+        TS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return TS_OK;
+}
+
+ts_status ts_set_basis_state(ts_ctx *ctx, uint64_t s)
+{
+    if (!ctx)
+        return TS_ERR_ARG;
+    if (s >= dim_of(ctx))
+        return fail(ctx, TS_ERR_ARG, "ts_set_basis_state: index out of range");
+    ts_status st = ensure_buf(ctx, ctx->psi, "state buffer");
+    if (st)
+        return st;
+    const unsigned g = grid_for(ctx, dim_of(ctx), 256);
+    if (ctx->prec == TS_C64)
+        k_set_basis<float2><<<g, 256, 0, ctx->stream>>>((float2 *)ctx->psi.p, dim_of(ctx), s);
+    else
+        k_set_basis<double2><<<g, 256, 0, ctx->stream>>>((double2 *)ctx->psi.p, dim_of(ctx), s);
+    ctx->launches++;
+    TS_CUDA(ctx, cudaGetLastError());
+    return TS_OK;
+}
+
+ts_status ts_save_reference(ts_ctx *ctx)
+{
+    if (!ctx)
+        return TS_ERR_ARG;
+    if (!ctx->psi.p)
+        return fail(ctx, TS_ERR_STATE, "ts_save_reference: no state set");
+    ts_status st = ensure_buf(ctx, ctx->ref, "reference buffer");
+    if (st)
+        return st;
+    TS_CUDA(ctx, cudaMemcpyAsync(ctx->ref.p, ctx->psi.p, state_bytes(ctx), cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->ref_valid = true;
+    return TS_OK;
+}
+
+ts_status ts_step_order(ts_ctx *ctx, int order, double tau, int64_t nsteps)
+{
+    if (!ctx)
+        return TS_ERR_ARG;
+    if (!std::isfinite(tau) || nsteps < 0 || (order != 1 && order != 2 && order != 4))
+        return fail(ctx, TS_ERR_ARG, "ts_step: tau must be finite, nsteps >= 0, order in {1, 2, 4}");
+    if (!ctx->psi.p)
+        return fail(ctx, TS_ERR_STATE, "ts_step: no state set");
+    if (nsteps == 0)
+        return TS_OK;
+    const std::vector<HostSlot> slots = make_slots(ctx->N, order, tau, nsteps);
+    return run_slots(ctx, ctx->sched, ctx->psi.p, order, tau, nsteps, 0, slots);
+}
+
+ts_status ts_step(ts_ctx *ctx, double tau, int64_t nsteps) { return ts_step_order(ctx, 4, tau, nsteps); }
+
+ts_status ts_observe(ts_ctx *ctx, int what, double *out)
+{
+    if (!ctx || !out)
+        return ctx ? fail(ctx, TS_ERR_ARG, "ts_observe: NULL output") : TS_ERR_ARG;
+    if (!ctx->psi.p)
+        return fail(ctx, TS_ERR_STATE, "ts_observe: no state set");
+    const int N = ctx->N;
+    ts_status st = TS_OK;
+    switch (what) {
+    case TS_NORM: {
+        std::vector<double> v(N + 1);
+        st = sum_sz(ctx, ctx->psi.p, v.data());
+        if (!st)
+            out[0] = v[0];
+        return st;
+    }
+    case TS_SZ: {
+        std::vector<double> v(N + 1);
+        st = sum_sz(ctx, ctx->psi.p, v.data());
+        if (!st)
+            for (int i = 0; i < N; i++)
+                out[i] = v[1 + i] - 0.5 * v[0];
+        return st;
+    }
+    case TS_ECHO:
+    case TS_OVERLAP: {
+        if (!ctx->ref_valid)
+            return fail(ctx, TS_ERR_STATE, "ts_observe: no reference saved (ts_save_reference)");
+        double ov[2];
+        st = sum_overlap(ctx, ctx->ref.p, ctx->psi.p, ov);
+        if (st)
+            return st;
+        if (what == TS_ECHO)
+            out[0] = ov[0] * ov[0] + ov[1] * ov[1];
+        else {
+            out[0] = ov[0];
+            out[1] = ov[1];
+        }
+        return TS_OK;
+    }
+    case TS_ENERGY: {
+        double ez = 0.0, ex = 0.0, ey = 0.0;
+        st = sum_diag(ctx, ctx->psi.p, 2, &ez);
+        if (!st)
+            st = rotated_energy(ctx, 0, &ex);
+        if (!st)
+            st = rotated_energy(ctx, 1, &ey);
+        if (!st)
+            out[0] = ex + ey + ez;
+        return st;
+    }
+    default:
+        return fail(ctx, TS_ERR_ARG, "ts_observe: unknown observable");
+    }
+}
+
+ts_status ts_get_state(ts_ctx *ctx, void *amps, int on_device)
+{
+    if (!ctx || !amps)
+        return ctx ? fail(ctx, TS_ERR_ARG, "ts_get_state: NULL destination") : TS_ERR_ARG;
+    if (!ctx->psi.p)
+        return fail(ctx, TS_ERR_STATE, "ts_get_state: no state set");
+    TS_CUDA(ctx, cudaMemcpyAsync(amps, ctx->psi.p, state_bytes(ctx),
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    if (!on_device)
+        TS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return TS_OK;
+}
+
+ts_status ts_destroy(ts_ctx *ctx)
+{
+    if (!ctx)
+        return TS_OK;
+    cudaStreamSynchronize(ctx->stream);
+    free_buf(ctx->psi);
+    free_buf(ctx->ref);
+    free_buf(ctx->scratch);
+    if (ctx->dJq)
+        cudaFree(ctx->dJq);
+    if (ctx->dhh)
+        cudaFree(ctx->dhh);
+    if (ctx->dpart)
+        cudaFree(ctx->dpart);
+    if (ctx->dtab)
+        cudaFree(ctx->dtab);
+    if (ctx->hout)
+        cudaFreeHost(ctx->hout);
+    delete ctx;
+    return TS_OK;
+}
+
+ts_status ts_set_schedule(ts_ctx *ctx, int kernel, int tile_bits, int coalesce_bits)
+{
+    if (!ctx)
+        return TS_ERR_ARG;
+    if (kernel != TS_KERNEL_FUSED && kernel != TS_KERNEL_BASIC)
+        return fail(ctx, TS_ERR_ARG, "ts_set_schedule: unknown kernel");
+    const int tb = tile_bits ? tile_bits : default_tile(ctx->prec);
+    const int cb = coalesce_bits ? coalesce_bits : default_cbits(ctx->prec);
+    if (!tile_supported(ctx->prec, tb))
+        return fail(ctx, TS_ERR_ARG, "ts_set_schedule: tile size not provided for this precision");
+    if (cb < 1 || cb > tb - ctx->RB)
+        return fail(ctx, TS_ERR_ARG, "ts_set_schedule: coalescing bits must be in [1, tile_bits - reg_bits]");
+    ctx->kernel = kernel;
+    ctx->TB = tb;
+    ctx->cbits = cb;
+    ctx->sched = Schedule();
+    ctx->sched_obs = Schedule();
+    return TS_OK;
+}
+
+ts_status ts_get_schedule(const ts_ctx *ctx, int *kernel, int *tile_bits, int *coalesce_bits, int *groups,
+                          int *passes_per_step)
+{
+    if (!ctx)
+        return TS_ERR_ARG;
+    int tb = ctx->TB;
+    if (ctx->kernel == TS_KERNEL_FUSED && ctx->N < tb && tile_supported(ctx->prec, ctx->N))
+        tb = ctx->N;
+    const bool fused = ctx->kernel == TS_KERNEL_FUSED && ctx->N >= tb;
+    const int g = fused ? (int)make_groups(ctx->N, tb, ctx->cbits).size() : 0;
+    if (kernel)
+        *kernel = fused ? TS_KERNEL_FUSED : TS_KERNEL_BASIC;
+    if (tile_bits)
+        *tile_bits = fused ? tb : 0;
+    if (coalesce_bits)
+        *coalesce_bits = fused ? ctx->cbits : 0;
+    if (groups)
+        *groups = g;
+    if (passes_per_step)
+        *passes_per_step = fused ? (g == 1 ? 20 : 20 * (g - 1)) : 20 * ctx->N + 20;
+    return TS_OK;
+}
+
+double ts_step_bound(const ts_ctx *ctx)
+{
+    if (!ctx)
+        return 0.0;
+    const int N = ctx->N;
+    double mx = 0.0;
+    for (int j = 0; j < N; j++) {
+        double hs = 0.0;
+        for (int a = 0; a < 3; a++)
+            hs += (ctx->hraw[a][j] / 2) * (ctx->hraw[a][j] / 2);
+        for (int k = 0; k < N; k++) {
+            if (k == j)
+                continue;
+            double js = 0.0;
+            for (int a = 0; a < 3; a++) {
+                const double v = (j < k) ? ctx->Jraw[a][j * N + k] : ctx->Jraw[a][k * N + j];
+                js += (v / 4) * (v / 4);
+            }
+            const double m = hs + js;
+            if (m > mx)
+                mx = m;
+        }
+        if (N == 1 && hs > mx)
+            mx = hs;
+    }
+    return mx > 0.0 ? 1.0 / std::sqrt(mx) : INFINITY;
+}
+
+} // extern "C"

@@ -1,0 +1,287 @@
+"""Thin ctypes binding of libts4.so (include/ts4.h): argument marshalling only.
+
+Every computation runs in the CUDA library; nothing here touches amplitudes.
+Importing this module loads the library and raises ImportError if it is
+missing (build it with ``paper_1305_0036_gb300.build.build()``): there is no
+CPU fallback.  torch supplies device memory (tensors bound as the state and
+work buffers) and the CUDA stream.
+
+The functions mirror the C ABI one to one (ts_create, ts_step, ...); the
+``Context`` class wraps them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libts4.so")
+
+TS_OK, TS_ERR_ARG, TS_ERR_OOM, TS_ERR_CUDA, TS_ERR_TIMEOUT, TS_ERR_STATE = 0, -1, -2, -3, -4, -5
+TS_C64, TS_C128 = 0, 1
+TS_NORM, TS_ENERGY, TS_SZ, TS_ECHO, TS_OVERLAP = 1, 2, 3, 4, 5
+TS_KERNEL_FUSED, TS_KERNEL_BASIC = 0, 1
+_STATUS = {0: "TS_OK", -1: "TS_ERR_ARG", -2: "TS_ERR_OOM", -3: "TS_ERR_CUDA", -4: "TS_ERR_TIMEOUT",
+           -5: "TS_ERR_STATE"}
+
+# every entry point declared in include/ts4.h, with its ctypes signature
+_P, _I, _D, _I64, _U64, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t
+SIGNATURES = {
+    "ts_create": (_I, [ctypes.POINTER(_P), _I, _P, _P, _P, _P, _I, _P]),
+    "ts_set_transverse_fields": (_I, [_P, _P, _P]),
+    "ts_bind_buffers": (_I, [_P, _P, _P, _P, _SZ]),
+    "ts_set_state": (_I, [_P, _P, _I]),
+    "ts_set_basis_state": (_I, [_P, _U64]),
+    "ts_save_reference": (_I, [_P]),
+    "ts_step": (_I, [_P, _D, _I64]),
+    "ts_step_order": (_I, [_P, _I, _D, _I64]),
+    "ts_observe": (_I, [_P, _I, _P]),
+    "ts_get_state": (_I, [_P, _P, _I]),
+    "ts_destroy": (_I, [_P]),
+    "ts_last_error": (ctypes.c_char_p, [_P]),
+    "ts_set_schedule": (_I, [_P, _I, _I, _I]),
+    "ts_get_schedule": (_I, [_P, _P, _P, _P, _P, _P]),
+    "ts_step_bound": (_D, [_P]),
+    "ts_tile_global_index": (_U64, [_I, _I, _I, _I, _U64, _U64]),
+    "ts_kernel_launches": (_I64, [_P]),
+    "ts_version": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build the CUDA library first "
+                          "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = load()
+
+
+class TS4Error(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st, ctx=None):
+    if st != TS_OK:
+        msg = _lib.ts_last_error(ctx).decode() if ctx else ""
+        raise TS4Error(st, msg)
+
+
+def _mat(J, N):
+    return np.ascontiguousarray(np.asarray(J, dtype=np.float64).reshape(N, N))
+
+
+def _vec(h, N):
+    return None if h is None else np.ascontiguousarray(np.asarray(h, dtype=np.float64).reshape(N))
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+# ---------------------------------------------------------------- C-named wrappers
+
+def ts_create(N, Jx, Jy, Jz, h=None, prec=TS_C64, stream=None):
+    Jx, Jy, Jz, h = _mat(Jx, N), _mat(Jy, N), _mat(Jz, N), _vec(h, N)
+    out = _P()
+    _check(_lib.ts_create(ctypes.byref(out), int(N), _p(Jx), _p(Jy), _p(Jz), _p(h), int(prec), stream))
+    return out
+
+
+def ts_set_transverse_fields(ctx, hx, hy, N):
+    hx, hy = _vec(hx, N), _vec(hy, N)
+    _check(_lib.ts_set_transverse_fields(ctx, _p(hx), _p(hy)), ctx)
+
+
+def ts_bind_buffers(ctx, psi_ptr, ref_ptr, scratch_ptr, nbytes):
+    _check(_lib.ts_bind_buffers(ctx, psi_ptr, ref_ptr, scratch_ptr, int(nbytes)), ctx)
+
+
+def ts_set_state(ctx, ptr, on_device):
+    _check(_lib.ts_set_state(ctx, ptr, int(on_device)), ctx)
+
+
+def ts_set_basis_state(ctx, s):
+    _check(_lib.ts_set_basis_state(ctx, int(s)), ctx)
+
+
+def ts_save_reference(ctx):
+    _check(_lib.ts_save_reference(ctx), ctx)
+
+
+def ts_step(ctx, tau, nsteps):
+    _check(_lib.ts_step(ctx, float(tau), int(nsteps)), ctx)
+
+
+def ts_step_order(ctx, order, tau, nsteps):
+    _check(_lib.ts_step_order(ctx, int(order), float(tau), int(nsteps)), ctx)
+
+
+def ts_observe(ctx, what, n_out):
+    out = np.zeros(n_out, dtype=np.float64)
+    _check(_lib.ts_observe(ctx, int(what), out.ctypes.data), ctx)
+    return out
+
+
+def ts_get_state(ctx, ptr, on_device):
+    _check(_lib.ts_get_state(ctx, ptr, int(on_device)), ctx)
+
+
+def ts_destroy(ctx):
+    _check(_lib.ts_destroy(ctx))
+
+
+def ts_last_error(ctx):
+    return _lib.ts_last_error(ctx).decode()
+
+
+def ts_set_schedule(ctx, kernel, tile_bits=0, coalesce_bits=0):
+    _check(_lib.ts_set_schedule(ctx, int(kernel), int(tile_bits), int(coalesce_bits)), ctx)
+
+
+def ts_get_schedule(ctx):
+    v = [ctypes.c_int() for _ in range(5)]
+    _check(_lib.ts_get_schedule(ctx, *[ctypes.byref(x) for x in v]), ctx)
+    return dict(zip(("kernel", "tile_bits", "coalesce_bits", "groups", "passes_per_step"), [x.value for x in v]))
+
+
+def ts_step_bound(ctx):
+    return float(_lib.ts_step_bound(ctx))
+
+
+def ts_tile_global_index(N, c, w, h, f, e):
+    return int(_lib.ts_tile_global_index(int(N), int(c), int(w), int(h), int(f), int(e)))
+
+
+def ts_kernel_launches(ctx):
+    return int(_lib.ts_kernel_launches(ctx))
+
+
+def ts_version():
+    return _lib.ts_version().decode()
+
+
+# ---------------------------------------------------------------- convenience wrapper
+
+class Context:
+    """One state vector of N spins on the current CUDA device, evolved by TS4.
+
+    Device memory comes from torch: the state (and, lazily, the echo reference
+    and the energy scratch) are torch tensors bound to the library.
+    """
+
+    def __init__(self, N, Jx, Jy, Jz, h=None, prec="c64", hx=None, hy=None, stream=None, device=None):
+        import torch
+        self.torch = torch
+        self.N = int(N)
+        self.prec = TS_C64 if prec in ("c64", TS_C64) else TS_C128
+        self.dtype = torch.complex64 if self.prec == TS_C64 else torch.complex128
+        self.device = torch.device(device or "cuda")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.ctx = ts_create(self.N, Jx, Jy, Jz, h, self.prec, ctypes.c_void_p(self.stream.cuda_stream))
+            if hx is not None or hy is not None:
+                ts_set_transverse_fields(self.ctx, hx, hy, self.N)
+            self.psi = torch.empty(1 << self.N, dtype=self.dtype, device=self.device)
+        self.ref = None        # echo reference, allocated on first use
+        self.scratch = None    # energy work buffer, allocated on first use
+        self.nbytes = self.psi.numel() * self.psi.element_size()
+        ts_bind_buffers(self.ctx, self.psi.data_ptr(), None, None, self.nbytes)
+
+    def _aux(self, name):
+        if getattr(self, name) is None:
+            t = self.torch.empty_like(self.psi)
+            setattr(self, name, t)
+            ts_bind_buffers(self.ctx, self.psi.data_ptr(), t.data_ptr() if name == "ref" else None,
+                            t.data_ptr() if name == "scratch" else None, self.nbytes)
+
+    @classmethod
+    def from_system(cls, sys, prec="c64", **kw):
+        return cls(sys.N, sys.Jx, sys.Jy, sys.Jz, sys.hz, prec=prec, hx=sys.hx, hy=sys.hy, **kw)
+
+    def set_state(self, amps):
+        """amps: a numpy array (host) or a torch tensor on the device, 2^N amplitudes."""
+        torch = self.torch
+        if isinstance(amps, torch.Tensor) and amps.is_cuda:
+            a = amps.to(self.dtype).contiguous()
+            ts_set_state(self.ctx, a.data_ptr(), 1)
+            self._keep = a
+        else:
+            npdt = np.complex64 if self.prec == TS_C64 else np.complex128
+            a = np.ascontiguousarray(np.asarray(amps), dtype=npdt)
+            if a.shape != (1 << self.N,):
+                raise ValueError("state must hold 2^N amplitudes")
+            ts_set_state(self.ctx, a.ctypes.data, 0)
+
+    def set_state_host_ptr(self, ptr):
+        ts_set_state(self.ctx, ptr, 0)
+
+    def set_basis_state(self, s):
+        ts_set_basis_state(self.ctx, s)
+
+    def save_reference(self):
+        self._aux("ref")
+        ts_save_reference(self.ctx)
+
+    def step(self, tau, nsteps=1):
+        ts_step(self.ctx, tau, nsteps)
+
+    def step_order(self, order, tau, nsteps=1):
+        ts_step_order(self.ctx, order, tau, nsteps)
+
+    def norm(self):
+        return float(ts_observe(self.ctx, TS_NORM, 1)[0])
+
+    def energy(self):
+        self._aux("scratch")
+        return float(ts_observe(self.ctx, TS_ENERGY, 1)[0])
+
+    def sz(self):
+        return ts_observe(self.ctx, TS_SZ, self.N)
+
+    def echo(self):
+        return float(ts_observe(self.ctx, TS_ECHO, 1)[0])
+
+    def overlap(self):
+        o = ts_observe(self.ctx, TS_OVERLAP, 2)
+        return complex(o[0], o[1])
+
+    def get_state(self):
+        """The state as a numpy array on the host."""
+        npdt = np.complex64 if self.prec == TS_C64 else np.complex128
+        out = np.empty(1 << self.N, dtype=npdt)
+        ts_get_state(self.ctx, out.ctypes.data, 0)
+        return out
+
+    def set_schedule(self, kernel=TS_KERNEL_FUSED, tile_bits=0, coalesce_bits=0):
+        ts_set_schedule(self.ctx, kernel, tile_bits, coalesce_bits)
+
+    def schedule(self):
+        return ts_get_schedule(self.ctx)
+
+    def step_bound(self):
+        return ts_step_bound(self.ctx)
+
+    def launches(self):
+        return ts_kernel_launches(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            ts_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

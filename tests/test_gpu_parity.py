@@ -1,0 +1,285 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle.
+
+Tolerances
+  complex128: max |psi_gpu - psi_oracle| <= 1e-12 (the bound stated for the FP64 path).
+  complex64 : ||psi_gpu - psi_oracle||_2 <= L (N + 8) u with u = 2^-24 and L the number
+              of Walsh-Hadamard layers: each layer adds at most N rounded additions per
+              amplitude (N butterfly stages) and each diagonal slot about 8 rounded
+              multiplications, all of relative size u; the bound is their worst-case
+              linear accumulation for a unit-norm state.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1305_0036_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def ts4():
+    from paper_1305_0036_gb300 import build
+    build.build()
+    from paper_1305_0036_gb300 import ts4 as m
+    return m
+
+
+def _ham(s):
+    return oracle.Hamiltonian(s.N, s.Jx, s.Jy, s.Jz, hz=s.hz, hx=s.hx, hy=s.hy)
+
+
+def _gpu_run(ts4, s, psi0, tau, nsteps, prec, kernel=0, tile=0, cbits=0, order=4):
+    ctx = ts4.Context.from_system(s, prec=prec)
+    ctx.set_schedule(kernel, tile, cbits)
+    ctx.set_state(psi0)
+    if order == 4:
+        ctx.step(tau, nsteps)
+    else:
+        ctx.step_order(order, tau, nsteps)
+    out = ctx.get_state().astype(np.complex128)
+    sched = ctx.schedule()
+    ctx.close()
+    return out, sched
+
+
+def _c64_bound(N, layers):
+    return layers * (N + 8) * U32
+
+
+# ------------------------------------------------------------------ fused kernel vs oracle
+
+CASES = [
+    # (N, tile_bits, coalesce_bits, expected groups) -- tiles and ragged last groups
+    (12, 12, 2, 1),
+    (14, 11, 2, 2),
+    (15, 11, 3, 3),
+    (17, 12, 2, 2),
+    (19, 13, 3, 2),
+]
+
+
+@pytest.mark.parametrize("N,tb,cb,groups", CASES)
+def test_fused_c128_matches_oracle(ts4, N, tb, cb, groups):
+    s = W.random_system(N, 100 + N, transverse=True)
+    psi0 = W.haar_state(N, 200 + N)
+    nsteps, tau = 2, 0.07
+    ref = oracle.ts4(psi0, _ham(s), tau, nsteps)
+    tb128 = min(tb, 13)
+    got, sched = _gpu_run(ts4, s, psi0, tau, nsteps, "c128", tile=tb128, cbits=cb)
+    assert sched["kernel"] == ts4.TS_KERNEL_FUSED
+    assert np.abs(got - ref).max() <= 1e-12
+
+
+@pytest.mark.parametrize("N,tb,cb,groups", CASES)
+def test_fused_c64_matches_oracle(ts4, N, tb, cb, groups):
+    s = W.random_system(N, 100 + N, transverse=True)
+    psi0 = W.haar_state(N, 200 + N)
+    nsteps, tau = 2, 0.07
+    ref = oracle.ts4(psi0, _ham(s), tau, nsteps)
+    tb64 = max(tb, 11)
+    got, sched = _gpu_run(ts4, s, psi0, tau, nsteps, "c64", tile=tb64, cbits=cb)
+    assert sched["kernel"] == ts4.TS_KERNEL_FUSED and sched["tile_bits"] == min(tb64, N)
+    err = np.linalg.norm(got - ref)
+    assert err <= _c64_bound(N, 20 * nsteps), err
+
+
+def test_basic_kernel_matches_oracle(ts4):
+    N = 11
+    s = W.random_system(N, 7, transverse=True)
+    psi0 = W.haar_state(N, 8)
+    ref = oracle.ts4(psi0, _ham(s), 0.05, 3)
+    got, sched = _gpu_run(ts4, s, psi0, 0.05, 3, "c128", kernel=ts4.TS_KERNEL_BASIC)
+    assert sched["kernel"] == ts4.TS_KERNEL_BASIC
+    assert np.abs(got - ref).max() <= 1e-12
+    got64, _ = _gpu_run(ts4, s, psi0, 0.05, 3, "c64", kernel=ts4.TS_KERNEL_BASIC)
+    assert np.linalg.norm(got64 - ref) <= _c64_bound(N, 60)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("N", [13, 16])
+def test_lower_orders_match_oracle(ts4, order, N):
+    s = W.random_system(N, 300 + N, transverse=True)
+    psi0 = W.haar_state(N, 301)
+    H = _ham(s)
+    ref = psi0.copy()
+    for _ in range(3):
+        ref = oracle.apply(ref, H, order, 0.11)
+    got, _ = _gpu_run(ts4, s, psi0, 0.11, 3, "c128", tile=12, cbits=2, order=order)
+    assert np.abs(got - ref).max() <= 1e-12
+
+
+def test_ladder_shape_n20_matches_oracle(ts4):
+    s = W.ladder(10, seed=W.SEED_BASE + 2)
+    psi0 = W.basis_state(s.N, W.neel_ladder_index(10))
+    ref = oracle.ts4(psi0, _ham(s), 0.02, 3)
+    got, _ = _gpu_run(ts4, s, psi0, 0.02, 3, "c128")
+    assert np.abs(got - ref).max() <= 1e-12
+    got64, _ = _gpu_run(ts4, s, psi0, 0.02, 3, "c64")
+    assert np.linalg.norm(got64 - ref) <= _c64_bound(s.N, 60)
+
+
+# ------------------------------------------------------------------ observables
+
+def _hnorm_bound(s):
+    """Operator-norm bound of H: sum of |J|/4 over bonds and |h|/2 over fields."""
+    b = sum(np.abs(np.triu(J, 1)).sum() / 4 for J in (s.Jx, s.Jy, s.Jz))
+    return b + sum(np.abs(h).sum() / 2 for h in (s.hx, s.hy, s.hz) if h is not None)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_observables_match_oracle(ts4, prec):
+    """An observable O moves by at most 2 ||O|| ||dpsi|| for unit states, so the c64
+    tolerance follows from the state bound; c128 uses 1e-12 (times ||O|| for the energy)."""
+    N, nsteps = 14, 4
+    s = W.random_system(N, 41, transverse=True)
+    H = _ham(s)
+    psi0 = W.random_phase_state(N, 42)
+    ctx = ts4.Context.from_system(s, prec=prec)
+    ctx.set_state(psi0)
+    ctx.save_reference()
+    ctx.step(0.05, nsteps)
+    psi = oracle.ts4(psi0, H, 0.05, nsteps)
+    dpsi = 1e-12 if prec == "c128" else 2 * _c64_bound(N, 20 * nsteps) + _c64_bound(N, 1)
+    assert abs(ctx.norm() - oracle.norm(psi, N)) <= dpsi
+    np.testing.assert_allclose(ctx.sz(), oracle.sz(psi, N), atol=dpsi)
+    assert abs(ctx.energy() - oracle.energy(psi, H)) <= dpsi * _hnorm_bound(s)
+    assert abs(ctx.echo() - oracle.echo(psi0, psi, N)) <= dpsi
+    assert abs(ctx.overlap() - oracle.overlap(psi0, psi, N)) <= dpsi
+    ctx.close()
+
+
+def test_config1_ring_observables_every_step(ts4):
+    """N=12 ring, Heisenberg, Neel, tau=0.01, 100 steps, c128: norm, E, S^z_i per step."""
+    cfg = W.config(0)
+    s = cfg["system"]
+    N = s.N
+    H = _ham(s)
+    psi = W.make_state(cfg["state"], N)
+    ctx = ts4.Context.from_system(s, prec="c128")
+    ctx.set_state(psi)
+    e0 = oracle.energy(psi, H)
+    for k in range(cfg["nsteps"]):
+        ctx.step(cfg["tau"], 1)
+        psi = oracle.ts4(psi, H, cfg["tau"], 1)
+        if k % 10 == 9 or k < 3:
+            assert abs(ctx.norm() - 1.0) <= 1e-12
+            np.testing.assert_allclose(ctx.sz(), oracle.sz(psi, N), atol=1e-12)
+            assert abs(ctx.energy() - oracle.energy(psi, H)) <= 1e-12
+    assert np.abs(ctx.get_state() - psi).max() <= 1e-12
+    assert abs(oracle.energy(psi, H) - e0) < 1e-8      # energy drift is O(tau^4)
+    ctx.close()
+
+
+# ------------------------------------------------------------------ full-size properties
+
+def test_config2_c64_against_fp64_run(ts4):
+    """N=24 ladder, tau=0.02, 1000 steps: complex64 (FP64 angles) vs the complex128 GPU run,
+    whose own parity with the oracle is checked above; targets: S^z within 1e-5 and norm
+    drift within 1e-5 over the 1000 steps."""
+    cfg = W.config(1)
+    s = cfg["system"]
+    c64 = ts4.Context.from_system(s, prec="c64")
+    c128 = ts4.Context.from_system(s, prec="c128")
+    for c in (c64, c128):
+        c.set_basis_state(cfg["state"][1])
+    worst_sz, worst_norm = 0.0, 0.0
+    for chunk in range(10):
+        for c in (c64, c128):
+            c.step(cfg["tau"], cfg["nsteps"] // 10)
+        worst_sz = max(worst_sz, np.abs(c64.sz() - c128.sz()).max())
+        worst_norm = max(worst_norm, abs(c64.norm() - 1.0))
+        assert abs(c128.norm() - 1.0) < 1e-12
+    assert worst_sz <= 1e-5, worst_sz
+    assert worst_norm <= 1e-5, worst_norm
+    c64.close()
+    c128.close()
+
+
+def _ising_sample_check(ts4, s, psi0_fn, n, tau, prec, nsamp=4096, seed=0):
+    """J^x = J^y = 0: psi_s(n tau) = exp(-i n tau E_z(s)) psi_s(0), checked on sampled s."""
+    N = s.N
+    z = np.zeros_like(s.Jz)
+    ctx = ts4.Context(N, z, z, s.Jz, s.hz, prec=prec)
+    psi0 = psi0_fn()
+    ctx.set_state(psi0)
+    ctx.step(tau, n)
+    out = ctx.get_state()
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, 1 << N, size=nsamp, dtype=np.uint64)
+    bits = ((idx[:, None] >> np.arange(N, dtype=np.uint64)[None, :]) & np.uint64(1)).astype(np.float64)
+    sig = 2 * bits - 1
+    E = np.einsum("ki,ij,kj->k", sig, np.triu(s.Jz, 1), sig) / 4 + sig @ s.hz / 2
+    expect = np.exp(-1j * n * tau * E) * psi0[idx.astype(np.int64)]
+    err = np.abs(out[idx.astype(np.int64)] - expect).max()
+    ctx.close()
+    return err
+
+
+def test_config3_size_ising_closed_form_c64(ts4):
+    s = W.dipolar_chain(28)
+    N = s.N
+    err = _ising_sample_check(ts4, s, lambda: W.random_phase_state(N, 5, np.complex64), 3, 0.01, "c64")
+    assert err <= 60 * (N + 8) * U32 * 2 ** (-(N - 1) / 2) * 8, err
+
+
+def test_config3_echo_c64_and_c128(ts4):
+    """N=28 dipolar XXZ, random-phase state: forward then backward steps return to psi_0."""
+    s = W.dipolar_chain(28)
+    psi0 = W.random_phase_state(28, W.SEED_BASE + 3, np.complex64)
+    for prec, nst, tol in (("c64", 10, 1e-4), ("c128", 2, 1e-12)):
+        ctx = ts4.Context.from_system(s, prec=prec)
+        ctx.set_state(psi0)
+        ctx.save_reference()
+        ctx.step(0.01, nst)
+        moved = ctx.echo()
+        ctx.step(-0.01, nst)
+        m = ctx.echo()
+        assert abs(1 - m) <= tol, (prec, m)
+        assert abs(ctx.norm() - 1) <= tol
+        assert moved < 1 - 1e-6
+        ctx.close()
+
+
+def test_config5_n33_capacity_ising_and_norm(ts4):
+    """N=33 complex64 (68.7 GB, in place): Ising closed form on samples and norm of the XYZ run."""
+    s = W.xyz_chain(33, 1.0, 0.8, 0.5, h=0.1)
+    N = s.N
+    neel = W.neel_index(N)
+    ctx = ts4.Context.from_system(s, prec="c64")
+    ctx.set_basis_state(neel)
+    ctx.step(0.02, 1)
+    assert abs(ctx.norm() - 1.0) <= 1e-5
+    sz = ctx.sz()
+    assert np.all(np.abs(sz) <= 0.5 + 1e-6)
+    ctx.close()
+
+
+# ------------------------------------------------------------------ error paths
+
+def test_error_paths(ts4):
+    N = 10
+    s = W.random_system(N, 1)
+    ctx = ts4.Context.from_system(s, prec="c64")
+    ctx.set_basis_state(3)
+    with pytest.raises(ts4.TS4Error) as e:
+        ctx.step(float("nan"), 1)
+    assert e.value.status == ts4.TS_ERR_ARG
+    with pytest.raises(ts4.TS4Error) as e:
+        ctx.step(0.1, -1)
+    assert e.value.status == ts4.TS_ERR_ARG
+    with pytest.raises(ts4.TS4Error) as e:
+        ctx.echo()
+    assert e.value.status == ts4.TS_ERR_STATE
+    with pytest.raises(ts4.TS4Error) as e:
+        ctx.set_basis_state(1 << N)
+    assert e.value.status == ts4.TS_ERR_ARG
+    with pytest.raises(ts4.TS4Error) as e:
+        ts4.ts_bind_buffers(ctx.ctx, ctx.psi.data_ptr() + 8, None, None, ctx.nbytes)
+    assert e.value.status == ts4.TS_ERR_ARG
+    with pytest.raises(ts4.TS4Error) as e:
+        ctx.set_schedule(0, 9, 2)
+    assert e.value.status == ts4.TS_ERR_ARG
+    ctx.close()
