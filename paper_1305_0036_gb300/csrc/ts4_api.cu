@@ -13,11 +13,12 @@
 //     (groups are visited in alternating order).  Passes per chained TS4 step:
 //     20 (g - 1).
 #include "../../include/ts4.h"
-#include "ts4_kernels.cuh"
+#include "ts4_tile.cuh"
 
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <string>
 #include <tuple>
@@ -60,6 +61,7 @@ struct HostPass {
     int slot = -1;      // slot index or -1
     int phase_k = 0;    // chunk of the step that applies the slot
     int tab = -1;
+    bool exact = false; // c64: per-amplitude factor through sincospif (large angles)
 };
 
 struct Schedule {
@@ -71,10 +73,31 @@ struct Schedule {
     // content
     std::vector<HostSlot> slots;
     std::vector<Group> groups;
+    std::vector<IOLayout> io;      // per group
     std::vector<HostPass> passes;
     std::vector<unsigned char> tabs;    // host image of the PassTab array
     size_t tab_size = 0;
+    void *dtab = nullptr;                // device copy, owned by this schedule
+    size_t dtab_cap = 0;
 };
+
+// Frees S's device tables once the stream's queued passes (which read them) are done.
+void release_tables(Schedule &S, cudaStream_t st)
+{
+    if (S.dtab) {
+        cudaStreamSynchronize(st);
+        cudaFree(S.dtab);
+    }
+    S.dtab = nullptr;
+    S.dtab_cap = 0;
+}
+
+// Drops the pass list and tables of S (keeps nothing cached).
+void reset_schedule(Schedule &S, cudaStream_t st)
+{
+    release_tables(S, st);
+    S = Schedule();
+}
 
 constexpr int kMaxN = 34;
 
@@ -96,8 +119,6 @@ struct ts_ctx {
     double *dpart = nullptr;
     size_t part_cap = 0;      // doubles
     double *hout = nullptr;   // pinned, kMaxN + 8 doubles
-    void *dtab = nullptr;
-    size_t tab_cap = 0;
     int kernel = TS_KERNEL_FUSED;
     int TB = 0, RB = 0, cbits = 0;
     Schedule sched;       // last ts_step schedule
@@ -138,39 +159,37 @@ size_t state_bytes(const ts_ctx *ctx) { return (size_t)dim_of(ctx) * amp_bytes(c
 int reg_bits(ts_prec p) { return p == TS_C64 ? 5 : 4; }
 bool tile_supported(ts_prec p, int tb)
 {
-    return p == TS_C64 ? (tb >= 11 && tb <= 14) : (tb >= 10 && tb <= 13);
+    return p == TS_C64 ? (tb >= 12 && tb <= 14) : (tb >= 11 && tb <= 13);
 }
-int default_tile(ts_prec p) { return p == TS_C64 ? 14 : 12; }
+int default_tile(ts_prec p) { return p == TS_C64 ? 13 : 12; }
 int default_cbits(ts_prec p) { return p == TS_C64 ? 3 : 2; }
 
 template <typename R, int TB, int RB>
-cudaError_t launch_pass_t(cudaStream_t st, void *psi, const PassArgs &a, const void *tabs, uint64_t nblk)
+cudaError_t launch_tile_t(cudaStream_t st, void *psi, const TileArgs &a, const void *tabs, uint64_t nblk)
 {
-    constexpr int NT = 1 << (TB - RB);
-    constexpr size_t smem = sizeof(typename CT<R>::T) << TB;
-    cudaError_t e = cudaFuncSetAttribute(k_pass<R, TB, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    using K = TileKernel<R, TB, RB>;
+    constexpr size_t smem = sizeof(typename CT<R>::T) * K::SMEM_ELEMS;
+    cudaError_t e = cudaFuncSetAttribute(k_tile<R, TB, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    k_pass<R, TB, RB><<<(unsigned)nblk, NT, smem, st>>>((typename CT<R>::T *)psi, a,
-                                                         (const PassTab<R, TB, RB> *)tabs);
+    k_tile<R, TB, RB><<<(unsigned)nblk, K::NT, smem, st>>>((typename CT<R>::T *)psi, a,
+                                                            (const TileTab<R, TB, RB> *)tabs);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pass(const ts_ctx *ctx, void *psi, const PassArgs &a, const void *tabs, uint64_t nblk)
+cudaError_t launch_tile(const ts_ctx *ctx, int TB, void *psi, const TileArgs &a, const void *tabs, uint64_t nblk)
 {
     if (ctx->prec == TS_C64) {
-        switch (ctx->TB) {
-        case 11: return launch_pass_t<float, 11, 5>(ctx->stream, psi, a, tabs, nblk);
-        case 12: return launch_pass_t<float, 12, 5>(ctx->stream, psi, a, tabs, nblk);
-        case 13: return launch_pass_t<float, 13, 5>(ctx->stream, psi, a, tabs, nblk);
-        default: return launch_pass_t<float, 14, 5>(ctx->stream, psi, a, tabs, nblk);
+        switch (TB) {
+        case 12: return launch_tile_t<float, 12, 5>(ctx->stream, psi, a, tabs, nblk);
+        case 13: return launch_tile_t<float, 13, 5>(ctx->stream, psi, a, tabs, nblk);
+        default: return launch_tile_t<float, 14, 5>(ctx->stream, psi, a, tabs, nblk);
         }
     }
-    switch (ctx->TB) {
-    case 10: return launch_pass_t<double, 10, 4>(ctx->stream, psi, a, tabs, nblk);
-    case 11: return launch_pass_t<double, 11, 4>(ctx->stream, psi, a, tabs, nblk);
-    case 12: return launch_pass_t<double, 12, 4>(ctx->stream, psi, a, tabs, nblk);
-    default: return launch_pass_t<double, 13, 4>(ctx->stream, psi, a, tabs, nblk);
+    switch (TB) {
+    case 11: return launch_tile_t<double, 11, 4>(ctx->stream, psi, a, tabs, nblk);
+    case 12: return launch_tile_t<double, 12, 4>(ctx->stream, psi, a, tabs, nblk);
+    default: return launch_tile_t<double, 13, 4>(ctx->stream, psi, a, tabs, nblk);
     }
 }
 
@@ -180,21 +199,23 @@ size_t tab_size(ts_prec p, int TB)
 {
     if (p == TS_C64) {
         switch (TB) {
-        case 11: return tab_size_t<float, 11, 5>();
         case 12: return tab_size_t<float, 12, 5>();
         case 13: return tab_size_t<float, 13, 5>();
         default: return tab_size_t<float, 14, 5>();
         }
     }
     switch (TB) {
-    case 10: return tab_size_t<double, 10, 4>();
     case 11: return tab_size_t<double, 11, 4>();
     case 12: return tab_size_t<double, 12, 4>();
     default: return tab_size_t<double, 13, 4>();
     }
 }
 
-// Host FP64 construction of one PassTab (A over the tile's local bits, QK for the slot's chunk).
+// Host FP64 construction of the per-(slot, group) tables of the tile kernel.
+//   c64 : A = t J/4 on the tile's local bits (radians); Q[j] = (hi, lo) float pair of
+//         q(j) = sum_{l<m in chunk} A_lm s_l s_m (radians); the i^{pcq popcount(j)} part is
+//         applied in the kernel.
+//   c128: A in half-turns; Q[j] = exp(-i q(j)) i^{pcq popcount(j)}.
 template <typename R, int TB, int RB>
 void build_tab_t(unsigned char *dst, const ts_ctx *ctx, const HostSlot &sl, const Group &g, int phase_k)
 {
@@ -209,9 +230,10 @@ void build_tab_t(unsigned char *dst, const ts_ctx *ctx, const HostSlot &sl, cons
         for (int m = 0; m < TB; m++)
             if (l != m)
                 A[l * TB + m] = sl.t * Jq[pos(l) * N + pos(m)];
+    const bool f32 = sizeof(R) == 4;
     for (int k = 0; k < TB * TB; k++)
-        tb.A[k] = (R)(A[k] / M_PI);
-    const int W = (phase_k * RB < TB - RB) ? phase_k * RB : TB - RB;
+        tb.A[k] = (R)(f32 ? A[k] : A[k] / M_PI);
+    const int W = chunk_w<TB, RB>(phase_k);
     for (int j = 0; j < (1 << RB); j++) {
         double q = 0.0;
         for (int l = 0; l < RB; l++)
@@ -220,37 +242,121 @@ void build_tab_t(unsigned char *dst, const ts_ctx *ctx, const HostSlot &sl, cons
                 const double sm_ = ((j >> m) & 1) ? 1.0 : -1.0;
                 q += A[(W + l) * TB + (W + m)] * sl_ * sm_;
             }
-        double re = std::cos(q), im = -std::sin(q);
-        const int k = (sl.pcq * __builtin_popcount((unsigned)j)) & 3;
-        for (int r = 0; r < k; r++) { // multiply by i
-            double t = re;
-            re = -im;
-            im = t;
-        }
         C z;
-        z.x = (R)re;
-        z.y = (R)im;
+        if (f32) {
+            z.x = (R)q;
+            z.y = (R)(q - (double)(float)q);
+        } else {
+            double re = std::cos(q), im = -std::sin(q);
+            const int k = (sl.pcq * __builtin_popcount((unsigned)j)) & 3;
+            for (int r = 0; r < k; r++) { // multiply by i
+                double t = re;
+                re = -im;
+                im = t;
+            }
+            z.x = (R)re;
+            z.y = (R)im;
+        }
         tb.QK[j] = z;
     }
     std::memcpy(dst, &tb, sizeof(tb));
 }
 
-void build_tab(unsigned char *dst, const ts_ctx *ctx, const HostSlot &sl, const Group &g, int phase_k)
+void build_tab(unsigned char *dst, const ts_ctx *ctx, int TB, const HostSlot &sl, const Group &g, int phase_k)
 {
     if (ctx->prec == TS_C64) {
-        switch (ctx->TB) {
-        case 11: return build_tab_t<float, 11, 5>(dst, ctx, sl, g, phase_k);
+        switch (TB) {
         case 12: return build_tab_t<float, 12, 5>(dst, ctx, sl, g, phase_k);
         case 13: return build_tab_t<float, 13, 5>(dst, ctx, sl, g, phase_k);
         default: return build_tab_t<float, 14, 5>(dst, ctx, sl, g, phase_k);
         }
     }
-    switch (ctx->TB) {
-    case 10: return build_tab_t<double, 10, 4>(dst, ctx, sl, g, phase_k);
+    switch (TB) {
     case 11: return build_tab_t<double, 11, 4>(dst, ctx, sl, g, phase_k);
     case 12: return build_tab_t<double, 12, 4>(dst, ctx, sl, g, phase_k);
     default: return build_tab_t<double, 13, 4>(dst, ctx, sl, g, phase_k);
     }
+}
+
+// Upper bound of |y_j| (radians) in the c64 per-amplitude factor of a slot on tile group g:
+// every per-thread coefficient is at most |t| (|h/2| + sum |J/4|) of its spin; RB of them
+// plus the in-chunk quadratic terms.
+double slot_y_bound(const ts_ctx *ctx, const HostSlot &sl, int RB)
+{
+    const int N = ctx->N;
+    const double *Jq = ctx->Jq.data() + (size_t)sl.alpha * N * N;
+    const double *hh = ctx->hh.data() + (size_t)sl.alpha * N;
+    double bmax = 0.0;
+    for (int i = 0; i < N; i++) {
+        double b = std::fabs(hh[i]);
+        for (int j = 0; j < N; j++)
+            b += std::fabs(Jq[i * N + j]);
+        bmax = std::max(bmax, b);
+    }
+    return std::fabs(sl.t) * bmax * RB * 2.0;
+}
+
+// I/O layout of a group.  The 5 lanes must hold the globally lowest bits of the
+// tile (the c lowest spins, then window spins when c < 5) so that one warp
+// instruction covers consecutive addresses; their order is free, and the first
+// 4 (3 for 16-byte amplitudes) are ordered to give distinct shared-memory bank
+// contributions, so that the transposes from and to this layout are
+// conflict-free whenever the bits allow it.
+IOLayout make_io(const Group &g, int TB, int RB, int ES, int io_chunk)
+{
+    IOLayout io;
+    std::memset(&io, 0, sizeof(io));
+    io.chunk = io_chunk;
+    const int W = io_chunk == 0 ? 0 : (RB < TB - RB ? RB : TB - RB);
+    auto gp = [&](int l) { return l < g.h ? g.w + l : l - g.h; };
+    auto contrib = [&](int k) {
+        const uint32_t e = 1u << k;
+        const uint32_t p = ES == 8 ? e + (e >> 5) + (e >> 10) : e + (e >> 4) + (e >> 8);
+        return (int)(p & (ES == 8 ? 15u : 7u));
+    };
+    std::vector<int> tb;
+    for (int l = 0; l < TB; l++)
+        if (l < W || l >= W + RB)
+            tb.push_back(l);
+    std::sort(tb.begin(), tb.end(), [&](int a, int b) { return gp(a) < gp(b); });
+    auto has = [](const std::vector<int> &v, int l) { return std::find(v.begin(), v.end(), l) != v.end(); };
+    // the lane set: contiguous bits first (lowest global positions), then window bits
+    // that add new bank contributions, then any
+    std::vector<int> set;
+    int seen = 0;
+    for (int l : tb)
+        if (gp(l) < g.c && (int)set.size() < 5) {
+            set.push_back(l);
+            seen |= contrib(l);
+        }
+    for (int l : tb)
+        if ((int)set.size() < 5 && !has(set, l) && contrib(l) && !(seen & contrib(l))) {
+            set.push_back(l);
+            seen |= contrib(l);
+        }
+    for (int l : tb)
+        if ((int)set.size() < 5 && !has(set, l))
+            set.push_back(l);
+    // order within the set: distinct nonzero contributions first
+    const int need = ES == 8 ? 4 : 3;
+    std::vector<int> lanes;
+    int got = 0;
+    for (int l : set)
+        if ((int)lanes.size() < need && contrib(l) && !(got & contrib(l))) {
+            lanes.push_back(l);
+            got |= contrib(l);
+        }
+    for (int l : set)
+        if (!has(lanes, l))
+            lanes.push_back(l);
+    int n = 0;
+    for (int l : lanes)
+        io.bits[n++] = (uint8_t)l;
+    std::vector<int> rest;
+    for (int l = 0; l < TB; l++)
+        if ((l < W || l >= W + RB) && !has(lanes, l))
+            io.bits[n++] = (uint8_t)l;
+    return io;
 }
 
 // ------------------------------------------------------------ slots (Sec. 2)
@@ -539,21 +645,26 @@ ts_status run_basic(ts_ctx *ctx, void *buf, const std::vector<HostSlot> &slots)
     return TS_OK;
 }
 
-// Builds (or reuses) the fused schedule for the given slots.
+// Builds the fused schedule for the slots in S: groups, passes, per-group I/O
+// layouts, and one table per distinct (slot values, group, phase chunk).
 ts_status prepare_fused(ts_ctx *ctx, Schedule &S)
 {
-    const int RB = ctx->RB;
-    S.groups = make_groups(ctx->N, ctx->TB, ctx->cbits);
+    const int RB = ctx->RB, TB = ctx->TB;
+    const int ES = (int)amp_bytes(ctx);
+    S.groups = make_groups(ctx->N, TB, ctx->cbits);
+    S.io.clear();
+    for (size_t gi = 0; gi < S.groups.size(); gi++)
+        S.io.push_back(make_io(S.groups[gi], TB, RB, ES, S.groups[gi].c == 0 ? 1 : 0));
     const int64_t L = (int64_t)S.slots.size() - 1;
-    S.passes = make_passes(S.groups, L, ctx->TB, RB);
-    // one table per distinct (slot values, group, phase chunk)
-    S.tab_size = tab_size(ctx->prec, ctx->TB);
+    S.passes = make_passes(S.groups, L, TB, RB);
+    S.tab_size = tab_size(ctx->prec, TB);
     std::map<std::tuple<double, int, int, int, int>, int> seen;
     S.tabs.clear();
     for (auto &p : S.passes) {
         if (p.slot < 0)
             continue;
         const HostSlot &sl = S.slots[p.slot];
+        p.exact = ctx->prec == TS_C64 && slot_y_bound(ctx, sl, RB) > 0.5;
         auto key = std::make_tuple(sl.t, sl.alpha, sl.pcq, p.group, p.phase_k);
         auto it = seen.find(key);
         if (it != seen.end()) {
@@ -564,18 +675,15 @@ ts_status prepare_fused(ts_ctx *ctx, Schedule &S)
         seen[key] = idx;
         p.tab = idx;
         S.tabs.resize((size_t)(idx + 1) * S.tab_size);
-        build_tab(S.tabs.data() + (size_t)idx * S.tab_size, ctx, sl, S.groups[p.group], p.phase_k);
+        build_tab(S.tabs.data() + (size_t)idx * S.tab_size, ctx, TB, sl, S.groups[p.group], p.phase_k);
     }
-    if (S.tabs.size() > ctx->tab_cap) {
-        if (ctx->dtab)
-            cudaFree(ctx->dtab);
-        ctx->dtab = nullptr;
-        ctx->tab_cap = 0;
-        TS_CUDA(ctx, cudaMalloc(&ctx->dtab, S.tabs.size()));
-        ctx->tab_cap = S.tabs.size();
+    if (S.tabs.size() > S.dtab_cap) {
+        release_tables(S, ctx->stream);
+        TS_CUDA(ctx, cudaMalloc(&S.dtab, S.tabs.size()));
+        S.dtab_cap = S.tabs.size();
     }
     if (!S.tabs.empty())
-        TS_CUDA(ctx, cudaMemcpyAsync(ctx->dtab, S.tabs.data(), S.tabs.size(), cudaMemcpyHostToDevice, ctx->stream));
+        TS_CUDA(ctx, cudaMemcpyAsync(S.dtab, S.tabs.data(), S.tabs.size(), cudaMemcpyHostToDevice, ctx->stream));
     // the host image must stay valid until the copy is done
     TS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return TS_OK;
@@ -586,7 +694,7 @@ ts_status run_fused(ts_ctx *ctx, void *buf, const Schedule &S)
     const HamDev hd = ham_dev(ctx);
     for (const auto &p : S.passes) {
         const Group &g = S.groups[p.group];
-        PassArgs a;
+        TileArgs a;
         std::memset(&a, 0, sizeof(a));
         a.c = g.c;
         a.w = g.w;
@@ -597,9 +705,11 @@ ts_status run_fused(ts_ctx *ctx, void *buf, const Schedule &S)
         if (p.slot >= 0)
             a.slot = S.slots[p.slot].dev();
         a.tab = p.tab < 0 ? 0 : p.tab;
+        a.exact_sincos = p.exact ? 1 : 0;
+        a.io = S.io[p.group];
         a.ham = hd;
         const uint64_t nblk = UINT64_C(1) << (ctx->N - (g.c + g.h));
-        cudaError_t e = launch_pass(ctx, buf, a, ctx->dtab, nblk);
+        cudaError_t e = launch_tile(ctx, ctx->TB, buf, a, S.dtab, nblk);
         ctx->launches++;
         if (e != cudaSuccess)
             return cuda_fail(ctx, e, "fused pass launch");
@@ -625,7 +735,12 @@ ts_status run_slots(ts_ctx *ctx, Schedule &S, void *buf, int order, double tau, 
         const bool hit = S.order == order && S.tau == tau && S.n == n && S.kernel == ctx->kernel &&
                          S.TB == ctx->TB && S.cbits == ctx->cbits && S.mode == mode;
         if (!hit) {
+            // keep the device table buffer for reuse, rebuild everything else
+            void *keep = S.dtab;
+            const size_t keep_cap = S.dtab_cap;
             S = Schedule();
+            S.dtab = keep;
+            S.dtab_cap = keep_cap;
             S.slots = slots;
             st = prepare_fused(ctx, S);
             if (st == TS_OK) {
@@ -637,7 +752,7 @@ ts_status run_slots(ts_ctx *ctx, Schedule &S, void *buf, int order, double tau, 
                 S.cbits = ctx->cbits;
                 S.mode = mode;
             } else {
-                S = Schedule();
+                reset_schedule(S, ctx->stream);
             }
         }
         if (st == TS_OK)
@@ -849,8 +964,8 @@ ts_status ts_set_transverse_fields(ts_ctx *ctx, const double *hx, const double *
     TS_CUDA(ctx, cudaMemcpyAsync(ctx->dhh, ctx->hh.data(), ctx->hh.size() * sizeof(double), cudaMemcpyHostToDevice,
                                  ctx->stream));
     TS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    ctx->sched = Schedule();
-    ctx->sched_obs = Schedule();
+    reset_schedule(ctx->sched, ctx->stream);
+    reset_schedule(ctx->sched_obs, ctx->stream);
     return TS_OK;
 }
 
@@ -1025,8 +1140,8 @@ ts_status ts_destroy(ts_ctx *ctx)
         cudaFree(ctx->dhh);
     if (ctx->dpart)
         cudaFree(ctx->dpart);
-    if (ctx->dtab)
-        cudaFree(ctx->dtab);
+    release_tables(ctx->sched, ctx->stream);
+    release_tables(ctx->sched_obs, ctx->stream);
     if (ctx->hout)
         cudaFreeHost(ctx->hout);
     delete ctx;
@@ -1048,8 +1163,8 @@ ts_status ts_set_schedule(ts_ctx *ctx, int kernel, int tile_bits, int coalesce_b
     ctx->kernel = kernel;
     ctx->TB = tb;
     ctx->cbits = cb;
-    ctx->sched = Schedule();
-    ctx->sched_obs = Schedule();
+    reset_schedule(ctx->sched, ctx->stream);
+    reset_schedule(ctx->sched_obs, ctx->stream);
     return TS_OK;
 }
 

@@ -398,12 +398,58 @@ template <int K> __device__ void block_sum(double (&v)[K], double *__restrict__ 
     __syncthreads();
 }
 
+// Per-thread sums over the 32 amplitudes p[j * stride], j < 32 (those with j < n):
+// tot = sum |psi|^2 and low[b] = sum over j with bit b of j set (b < 5).
+// complex64: squares and pairwise sums in FP32 (error <= 5 u of the thread's
+// total), converted once to FP64; complex128: FP64 throughout.
+template <typename C, typename A>
+__device__ __forceinline__ void thread_sums32(const C *__restrict__ p, int stride, int n, double &tot,
+                                              double (&low)[5])
+{
+    A q[32];
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+        C a;
+        a.x = 0;
+        a.y = 0;
+        if (j < n)
+            a = p[(size_t)j * stride];
+        q[j] = (A)a.x * (A)a.x + (A)a.y * (A)a.y;
+    }
+    // sum over the elements with bit b set = pairwise tree over the 16 such elements
+#pragma unroll
+    for (int b = 0; b < 5; b++) {
+        A t[16];
+        int k = 0;
+#pragma unroll
+        for (int j = 0; j < 32; j++)
+            if ((j >> b) & 1)
+                t[k++] = q[j];
+#pragma unroll
+        for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+            for (int i = 0; i < w; i++)
+                t[i] = t[i] + t[i + w];
+        low[b] = (double)t[0];
+    }
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1)
+#pragma unroll
+        for (int i = 0; i < w; i++)
+            q[i] = q[i] + q[i + w];
+    tot = (double)q[0];
+}
+
+template <typename C> struct AccOf;
+template <> struct AccOf<float2> { using T = float; };
+template <> struct AccOf<double2> { using T = double; };
+
 // Per block: [0] = sum |psi|^2, [1..] = sum |psi_s|^2 bit_i(s) for i < N  (stride N+1)
 template <typename C>
-__global__ void k_sum_sz(const C *__restrict__ psi, int N, double *__restrict__ part)
+__global__ void __launch_bounds__(256) k_sum_sz(const C *__restrict__ psi, int N, double *__restrict__ part)
 {
     // each block iteration covers a contiguous range of 2^13 amplitudes (256 threads x 32)
-    constexpr int LB = 5;                 // amplitudes per thread: 2^LB
+    constexpr int LB = 5;
     const uint64_t dim = UINT64_C(1) << N;
     __shared__ double acc_sh[64];
     for (int i = threadIdx.x; i < 64; i += blockDim.x)
@@ -411,30 +457,26 @@ __global__ void k_sum_sz(const C *__restrict__ psi, int N, double *__restrict__ 
     __syncthreads();
     const uint64_t per_block = (uint64_t)blockDim.x << LB;
     const int RBITS = 5 + 8;              // bits resolved inside one block range (blockDim = 256)
+    // amplitude base + (j << 8) + tid: thread bits are global bits 0..7 (coalesced),
+    // the 32 per-thread values are global bits 8..12
     for (uint64_t base = (uint64_t)blockIdx.x * per_block; base < dim; base += (uint64_t)gridDim.x * per_block) {
         double tot = 0.0, low[LB] = {0, 0, 0, 0, 0};
-        const uint64_t s0 = base + ((uint64_t)threadIdx.x << LB);
+        const uint64_t s0 = base + threadIdx.x;
         if (s0 < dim) {
-            const int n = (dim - s0 < (1u << LB)) ? (int)(dim - s0) : (1 << LB);
-            for (int j = 0; j < n; j++) {
-                const double p = norm2(psi[s0 + j]);
-                tot += p;
-#pragma unroll
-                for (int b = 0; b < LB; b++)
-                    if ((j >> b) & 1)
-                        low[b] += p;
-            }
+            const uint64_t rem = (dim - s0 + 255) >> 8;       // elements s0 + 256 j below dim
+            const int n = rem < 32 ? (int)rem : 32;
+            thread_sums32<C, typename AccOf<C>::T>(psi + s0, 256, n, tot, low);
         }
-        double v[1 + LB + 8];
+        double v[1 + 8 + LB];
         v[0] = tot;
 #pragma unroll
-        for (int b = 0; b < LB; b++)
-            v[1 + b] = low[b];
-#pragma unroll
         for (int b = 0; b < 8; b++)
-            v[1 + LB + b] = ((threadIdx.x >> b) & 1) ? tot : 0.0;
-        __shared__ double bs[1 + LB + 8];
-        block_sum<1 + LB + 8>(v, bs);
+            v[1 + b] = ((threadIdx.x >> b) & 1) ? tot : 0.0;
+#pragma unroll
+        for (int b = 0; b < LB; b++)
+            v[1 + 8 + b] = low[b];
+        __shared__ double bs[1 + 8 + LB];
+        block_sum<1 + 8 + LB>(v, bs);
         if (threadIdx.x == 0) {
             acc_sh[0] += bs[0];
             for (int i = 0; i < N && i < RBITS; i++)

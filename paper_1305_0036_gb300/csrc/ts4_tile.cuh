@@ -1,0 +1,515 @@
+// Fused tile pass, register-resident (Secs. 3.3-3.4 redesigned for sm_103a).
+//
+// A thread block owns one tile of 2^TB amplitudes: the tile's local bits are the
+// window spins [w, w + h) (local bits [0, h)) and the c = TB - h lowest spins
+// (local bits [h, TB)); the block index fixes every other spin.  Each thread
+// keeps 2^RB amplitudes in registers.  A "layout" says which RB local bits are
+// the register index; the others are spread over the 32 lanes and the warps.
+// Butterflies on register bits need no data movement; to rotate other bits the
+// tile is transposed to another layout through shared memory.
+//
+// Layouts: chunk k holds the local bits [W_k, W_k + RB), W_k = min(k RB, TB - RB).
+// One chunk (1 for the lowest-spin group, 0 for the others) is also the I/O
+// layout: its lanes are chosen (on the host) among the globally lowest bits of
+// the tile so that the global loads and stores of one warp instruction cover
+// consecutive addresses.
+//
+// Shared memory holds the transposed tile at padded positions
+//   P(e) = e + (e >> 5) + (e >> 10)        (8-byte amplitudes, bank pair P mod 16)
+//   P(e) = e + (e >> 4) + (e >> 8)         (16-byte amplitudes, 16-byte slot P mod 8)
+// P is additive over disjoint bit sets, so the address of register j is the
+// thread's base plus a compile-time offset, and the lanes of every layout are
+// chosen so that the bank contributions of their low bits are distinct powers
+// of two: every warp access is conflict-free.
+#pragma once
+
+#include "ts4_kernels.cuh"
+
+#include <type_traits>
+
+namespace ts4 {
+
+template <int ES> __host__ __device__ constexpr uint32_t padidx(uint32_t e)
+{
+    return ES == 8 ? e + (e >> 5) + (e >> 10) : e + (e >> 4) + (e >> 8);
+}
+template <int ES> __host__ __device__ constexpr int bank_contrib(int k)
+{
+    return (int)(padidx<ES>(1u << k) & (ES == 8 ? 15u : 7u));
+}
+
+// Thread-bit order (lanes first, then warps) of chunk layout W: the first
+// (ES == 8 ? 4 : 3) lane bits take distinct nonzero bank contributions.
+template <int TB, int RB, int ES> struct ChunkLayout {
+    int bits[TB - RB];
+    __host__ __device__ constexpr ChunkLayout(int W) : bits{}
+    {
+        const int need = ES == 8 ? 4 : 3;
+        bool used[32] = {};
+        int n = 0;
+        int seen = 0;  // bitmask of contributions taken
+        for (int k = 0; k < TB && n < need; k++) {
+            if (k >= W && k < W + RB)
+                continue;
+            const int cb = bank_contrib<ES>(k);
+            if (cb != 0 && !(seen & cb)) {
+                seen |= cb;
+                bits[n++] = k;
+                used[k] = true;
+            }
+        }
+        for (int k = 0; k < TB; k++) {
+            if ((k >= W && k < W + RB) || used[k])
+                continue;
+            bits[n++] = k;
+        }
+    }
+};
+
+template <int TB, int RB> __host__ __device__ constexpr int chunk_w(int k)
+{
+    return (k * RB < TB - RB) ? k * RB : TB - RB;
+}
+
+// I/O layout (the register bits of chunk `chunk`), computed on the host for each group.
+struct IOLayout {
+    uint8_t bits[16];   // thread bit t -> local bit (lanes first)
+    int chunk;          // 0 or 1
+};
+
+struct TileArgs {
+    int c, w, h;
+    int nsteps;
+    StepDesc steps[kMaxSteps];
+    Slot slot;
+    int has_slot;
+    int tab;
+    int exact_sincos;   // c64: use sincospif for the per-amplitude factor (|y| may exceed 0.5)
+    IOLayout io;
+    HamDev ham;
+};
+
+// Per-(slot, group) tables (host, FP64):
+//   c64 : A = t J / 4 on local bits (radians); Q[j] = (hi, lo) of the in-chunk quadratic term (radians)
+//   c128: A in half-turns; Q[j] = exp(-i q(j)) i^{pcq popcount(j)} (as in PassTab)
+template <typename R, int TB, int RB> using TileTab = PassTab<R, TB, RB>;
+
+struct SlotThreadC64 {
+    float2 T;
+    float Lo[8];
+    float Hi[4];
+    int pcq;
+};
+
+struct SlotThreadC128 {
+    double2 flo[4];
+    double2 fhi[4];
+};
+
+template <typename R, int TB, int RB> struct TileShared {
+    // per-thread slot factors, computed before the tile occupies the registers
+    typename std::conditional<sizeof(R) == 4, SlotThreadC64, SlotThreadC128>::type th_f[1 << (TB - RB)];
+    R A[TB * TB];
+    R g[TB];
+    typename CT<R>::T Q[1 << RB];
+    float th_hi, th_lo;  // c64: block angle in half-turns as a float pair
+    double th;           // c128: block angle in half-turns
+    int pcF;
+};
+
+__device__ __forceinline__ float2 two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    const float err = (a - (s - bb)) + (b - bb);
+    return make_float2(s, err);
+}
+
+// e^{-iy} for |y| <= 0.5 from the Taylor series of cos and sin (truncation < 1e-12)
+__device__ __forceinline__ float2 cexpm_small(float y)
+{
+    const float y2 = y * y;
+    float c = fmaf(y2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+    c = fmaf(y2, c, -1.0f / 720.0f);
+    c = fmaf(y2, c, 1.0f / 24.0f);
+    c = fmaf(y2, c, -0.5f);
+    c = fmaf(y2, c, 1.0f);
+    float s = fmaf(y2, -1.0f / 39916800.0f, 1.0f / 362880.0f);
+    s = fmaf(y2, s, -1.0f / 5040.0f);
+    s = fmaf(y2, s, 1.0f / 120.0f);
+    s = fmaf(y2, s, -1.0f / 6.0f);
+    s = fmaf(y2, s, 1.0f);
+    return make_float2(c, -y * s);
+}
+
+__host__ __device__ constexpr int popc_c(int v) { return v ? (v & 1) + popc_c(v >> 1) : 0; }
+
+// a * i^k for a run-time k, without branches: swap for odd k, negate for k = 2, 3
+__device__ __forceinline__ float2 rot_ipow(float2 a, int k)
+{
+    const bool odd = k & 1;
+    const float sg = (k & 2) ? -1.0f : 1.0f;
+    const float rx = odd ? -a.y : a.x;
+    const float ry = odd ? a.x : a.y;
+    return make_float2(sg * rx, sg * ry);
+}
+
+// c64 slot, one factor per amplitude:
+//   F(j) = T_thread * e^{-i y_j} * i^{pcq popcount(j)},
+//   T_thread = 2^{-e} i^{pcq (pcF + popcount(base))} e^{-i pi X}, X = block + thread angle
+//   y_j = sum_b s_b(j) c_b + q(j)  (small: |y| <= 0.5 unless exact_sincos)
+// Rounding happens per amplitude (no table of rounded factors shared by many
+// amplitudes), so the errors do not build up coherently over the steps.
+
+// Per-thread part (one copy for every layout: W is a run-time value).
+template <int TB, int RB>
+__device__ __forceinline__ void slot_thread_c64(SlotThreadC64 &o, uint32_t base, int W,
+                                             const TileShared<float, TB, RB> &sh, int pcq, float scale)
+{
+    float sacc = 0.0f;
+    float cb[RB];
+#pragma unroll
+    for (int b = 0; b < RB; b++)
+        cb[b] = sh.g[W + b];
+    const uint32_t chunk = ((1u << RB) - 1u) << W;
+    for (int m = 0; m < TB; m++) {
+        if ((chunk >> m) & 1u)
+            continue;
+        const float sm = ((base >> m) & 1u) ? 1.0f : -1.0f;
+        sacc = fmaf(sm, sh.g[m], sacc);
+        for (int l = m + 1; l < TB; l++) {
+            if ((chunk >> l) & 1u)
+                continue;
+            const float sl = ((base >> l) & 1u) ? sm : -sm;
+            sacc = fmaf(sl, sh.A[m * TB + l], sacc);
+        }
+#pragma unroll
+        for (int b = 0; b < RB; b++)
+            cb[b] = fmaf(sm, sh.A[(W + b) * TB + m], cb[b]);
+    }
+    // thread angle in half-turns, reduced exactly: X = th_hi + th_lo + sacc / pi
+    const float2 s1 = two_sum(sh.th_hi, sacc * 0.31830988618379067f);
+    const float q = rintf(2.0f * s1.x);
+    const float r = fmaf(-0.5f, q, s1.x) + (s1.y + sh.th_lo);
+    float sn, cs;
+    sincospif(r, &sn, &cs);
+    const int kt = (pcq * (sh.pcF + __popc(base)) - (int)q) & 3;
+    o.T = cmul_ipow(make_float2(cs * scale, -sn * scale), kt);
+    o.Lo[0] = 0.0f;
+#pragma unroll
+    for (int b = 0; b < 3; b++)
+#pragma unroll
+        for (int k = 0; k < (1 << b); k++) {
+            const float v = o.Lo[k];
+            o.Lo[k] = v - cb[b];
+            o.Lo[k | (1 << b)] = v + cb[b];
+        }
+    o.Hi[0] = -cb[3] - cb[4];
+    o.Hi[1] = cb[3] - cb[4];
+    o.Hi[2] = -cb[3] + cb[4];
+    o.Hi[3] = cb[3] + cb[4];
+    o.pcq = pcq;
+}
+
+template <int RB>
+__device__ __forceinline__ void slot_c64(float2 (&x)[1 << RB], const SlotThreadC64 &o, const float2 *__restrict__ Q,
+                                         bool exact)
+{
+    const int pcq = o.pcq;
+#pragma unroll
+    for (int j = 0; j < (1 << RB); j++) {
+        const float2 qv = Q[j];
+        const float y = ((o.Lo[j & 7] + o.Hi[j >> 3]) + qv.x) + qv.y;
+        float2 E;
+        if (!exact) {
+            E = cexpm_small(y);
+        } else {
+            float s2, c2;
+            sincospif(y * 0.31830988618379067f, &s2, &c2);
+            E = make_float2(c2, -s2);
+        }
+        x[j] = cmul(x[j], cmul(o.T, rot_ipow(E, (pcq * popc_c(j)) & 3)));
+    }
+}
+
+// c128 slot: per-thread factors (errors ~1e-16; table of the in-chunk terms).
+template <int TB, int RB>
+__device__ __forceinline__ void slot_thread_c128(SlotThreadC128 &o, uint32_t base, int W,
+                                                 const TileShared<double, TB, RB> &sh, int pcq, double scale)
+{
+    double ang = sh.th;
+    double cb[RB];
+#pragma unroll
+    for (int b = 0; b < RB; b++)
+        cb[b] = sh.g[W + b];
+    const uint32_t chunk = ((1u << RB) - 1u) << W;
+    for (int m = 0; m < TB; m++) {
+        if ((chunk >> m) & 1u)
+            continue;
+        const double sm = ((base >> m) & 1u) ? 1.0 : -1.0;
+        ang = fma(sm, sh.g[m], ang);
+        for (int l = m + 1; l < TB; l++) {
+            if ((chunk >> l) & 1u)
+                continue;
+            const double sl = ((base >> l) & 1u) ? sm : -sm;
+            ang = fma(sl, sh.A[m * TB + l], ang);
+        }
+#pragma unroll
+        for (int b = 0; b < RB; b++)
+            cb[b] = fma(sm, sh.A[(W + b) * TB + m], cb[b]);
+    }
+    double2 eb = cexpm_pi(ang);
+    eb.x *= scale;
+    eb.y *= scale;
+    eb = cmul_ipow(eb, pcq * (sh.pcF + __popc(base)));
+    static_assert(RB == 4, "c128 factors assume 4 register bits");
+    o.flo[0] = eb;
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+        const double2 ub = cexpm_pi(cb[b]);
+#pragma unroll
+        for (int k = 0; k < (1 << b); k++) {
+            const double2 v = o.flo[k];
+            o.flo[k] = cmul(v, cconj(ub));
+            o.flo[k | (1 << b)] = cmul(v, ub);
+        }
+    }
+    const double2 a1 = cexpm_pi(cb[2]), b1 = cexpm_pi(cb[3]);
+    const double2 a0 = cconj(a1), b0 = cconj(b1);
+    o.fhi[0] = cmul(a0, b0);
+    o.fhi[1] = cmul(a1, b0);
+    o.fhi[2] = cmul(a0, b1);
+    o.fhi[3] = cmul(a1, b1);
+}
+
+__device__ __forceinline__ void slot_c128(double2 (&x)[16], const SlotThreadC128 &o, const double2 *__restrict__ Q)
+{
+#pragma unroll
+    for (int j = 0; j < 16; j++)
+        x[j] = cmul(x[j], cmul(cmul(o.flo[j & 3], o.fhi[j >> 2]), Q[j]));
+}
+
+template <typename R, int TB, int RB> struct TileKernel {
+    using C = typename CT<R>::T;
+    static constexpr int ES = sizeof(C);
+    static constexpr int NT = 1 << (TB - RB);
+    static constexpr int NR = 1 << RB;
+    static constexpr int NTB = TB - RB;                // thread bits
+    static constexpr int NCH = (TB + RB - 1) / RB;     // chunks
+    static constexpr uint32_t SMEM_ELEMS = padidx<ES>((1u << TB) - 1) + 1;
+
+    // local base index of this thread in chunk layout K (K != 1)
+    template <int K> static __device__ __forceinline__ uint32_t chunk_base(uint32_t tid)
+    {
+        constexpr ChunkLayout<TB, RB, ES> L(chunk_w<TB, RB>(K));
+        uint32_t b = 0;
+#pragma unroll
+        for (int t = 0; t < NTB; t++)
+            b |= ((tid >> t) & 1u) << L.bits[t];
+        return b;
+    }
+
+    template <int K> static __device__ __forceinline__ void store_chunk(C *sm, uint32_t pbase, const C (&x)[NR])
+    {
+        constexpr int W = chunk_w<TB, RB>(K);
+#pragma unroll
+        for (int j = 0; j < NR; j++)
+            sm[pbase + padidx<ES>((uint32_t)j << W)] = x[j];
+    }
+    template <int K> static __device__ __forceinline__ void load_chunk(const C *sm, uint32_t pbase, C (&x)[NR])
+    {
+        constexpr int W = chunk_w<TB, RB>(K);
+#pragma unroll
+        for (int j = 0; j < NR; j++)
+            x[j] = sm[pbase + padidx<ES>((uint32_t)j << W)];
+    }
+
+    static __device__ __forceinline__ void apply_slot(C (&x)[NR], const TileShared<R, TB, RB> &sh, bool exact)
+    {
+        if constexpr (sizeof(R) == 4)
+            slot_c64<RB>(x, sh.th_f[threadIdx.x], sh.Q, exact);
+        else
+            slot_c128(x, sh.th_f[threadIdx.x], sh.Q);
+    }
+};
+
+template <typename R, int TB, int RB>
+__global__ void __launch_bounds__(1 << (TB - RB), (TB - RB <= 8) ? 2 : 1)
+k_tile(typename CT<R>::T *__restrict__ psi, const __grid_constant__ TileArgs a,
+       const TileTab<R, TB, RB> *__restrict__ tabs)
+{
+    using K = TileKernel<R, TB, RB>;
+    using C = typename CT<R>::T;
+    constexpr int NR = K::NR, NTB = K::NTB, ES = K::ES;
+    const int kio = a.io.chunk;
+    const int Wio = kio == 0 ? 0 : chunk_w<TB, RB>(1);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    __shared__ TileShared<R, TB, RB> sh;
+
+    const uint32_t tid = threadIdx.x;
+    const uint64_t f = blockIdx.x;
+    const int c = a.c, w = a.w, h = a.h;
+    const uint64_t gbase = tile_global_index(c, w, h, f, 0);
+
+    // ---- I/O layout: this thread's local base and its global offsets
+    uint32_t base_io = 0;
+#pragma unroll
+    for (int t = 0; t < NTB; t++)
+        base_io |= ((tid >> t) & 1u) << a.io.bits[t];
+    auto gpos = [&](int l) { return l < h ? w + l : l - h; };
+    uint64_t gthr = gbase;
+#pragma unroll
+    for (int t = 0; t < NTB; t++)
+        if ((tid >> t) & 1u)
+            gthr |= UINT64_C(1) << gpos(a.io.bits[t]);
+    uint64_t gst[RB];
+#pragma unroll
+    for (int b = 0; b < RB; b++)
+        gst[b] = UINT64_C(1) << gpos(Wio + b);
+
+    const uint32_t b0 = kio == 0 ? base_io : K::template chunk_base<0>(tid);
+    const uint32_t b1 = kio == 1 ? base_io : K::template chunk_base<1>(tid);
+    const uint32_t b2 = (K::NCH > 2) ? K::template chunk_base<2>(tid) : 0u;
+    const uint32_t b3 = (K::NCH > 3) ? K::template chunk_base<3>(tid) : 0u;
+    auto base_of = [&](int k) { return k == 0 ? b0 : k == 1 ? b1 : k == 2 ? b2 : b3; };
+    // ---- issue the tile's loads first: the slot set-up below runs under their latency
+    C x[NR];
+#pragma unroll
+    for (int j = 0; j < NR; j++) {
+        uint64_t gi = gthr;
+#pragma unroll
+        for (int b = 0; b < RB; b++)
+            if ((j >> b) & 1)
+                gi |= gst[b];
+        x[j] = __ldcs(psi + gi);
+    }
+
+    // ---- per-block part of the slot, FP64
+    int pcq = 0;
+    R scale = R(1);
+    const bool exact = a.exact_sincos != 0;
+    if (a.has_slot) {
+        const int N = a.ham.N;
+        const int al = a.slot.alpha;
+        const double t = a.slot.t;
+        const double *Jq = a.ham.Jq + (size_t)al * N * N;
+        const double *hh = a.ham.hh + (size_t)al * N;
+        pcq = a.slot.pcq;
+        scale = (R)ldexp(a.slot.mag, -a.slot.scale_exp);
+        // g in radians (c64) or half-turns (c128)
+        const double gunit = (sizeof(R) == 4) ? 1.0 : 0.31830988618379067153776752674503;
+        if (tid < TB) {
+            const int pos = gpos(tid);
+            double acc = hh[pos];
+            for (int j = 0; j < N; j++)
+                if (!in_tile(j, c, w, h))
+                    acc += Jq[pos * N + j] * (((gbase >> j) & 1) ? 1.0 : -1.0);
+            sh.g[tid] = (R)(t * acc * gunit);
+        } else if (tid >= 32 && tid < 64) {
+            const int lane = tid - 32;
+            double acc = 0.0;
+            for (int i = lane; i < N; i += 32) {
+                if (in_tile(i, c, w, h))
+                    continue;
+                double r = hh[i];
+                for (int j = i + 1; j < N; j++)
+                    if (!in_tile(j, c, w, h))
+                        r += Jq[i * N + j] * (((gbase >> j) & 1) ? 1.0 : -1.0);
+                acc += (((gbase >> i) & 1) ? 1.0 : -1.0) * r;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) {
+                const double th = halfturns_2pi(t * acc + a.slot.th0);
+                sh.th = th;
+                sh.th_hi = (float)th;
+                sh.th_lo = (float)(th - (double)(float)th);
+                sh.pcF = __popcll(gbase);
+            }
+        }
+        const TileTab<R, TB, RB> *tb = tabs + a.tab;
+        for (int k = tid; k < TB * TB; k += K::NT)
+            sh.A[k] = tb->A[k];
+        if (tid < NR)
+            sh.Q[tid] = tb->QK[tid];
+    }
+    __syncthreads();
+
+    // ---- per-thread slot factors, computed before the tile occupies the registers
+    if (a.has_slot) {
+        int kph = 0;
+        for (int s = 0; s < a.nsteps; s++)
+            if (a.steps[s].ph)
+                kph = a.steps[s].k;
+        if constexpr (sizeof(R) == 4)
+            slot_thread_c64<TB, RB>(sh.th_f[tid], base_of(kph), chunk_w<TB, RB>(kph), sh, pcq, (float)scale);
+        else
+            slot_thread_c128<TB, RB>(sh.th_f[tid], base_of(kph), chunk_w<TB, RB>(kph), sh, pcq, (double)scale);
+    }
+
+    // ---- steps: transpose to the step's chunk layout when it changes
+    int cur = kio;
+    for (int s = 0; s < a.nsteps; s++) {
+        const StepDesc d = a.steps[s];
+        const int k = d.k;
+        if (k != cur) {
+            __syncthreads();
+            const uint32_t pc = padidx<ES>(base_of(cur));
+            switch (cur) {
+            case 0: K::template store_chunk<0>(sm, pc, x); break;
+            case 1: K::template store_chunk<1>(sm, pc, x); break;
+            case 2: K::template store_chunk<2>(sm, pc, x); break;
+            default: K::template store_chunk<3>(sm, pc, x); break;
+            }
+            __syncthreads();
+            const uint32_t pn = padidx<ES>(base_of(k));
+            switch (k) {
+            case 0: K::template load_chunk<0>(sm, pn, x); break;
+            case 1: K::template load_chunk<1>(sm, pn, x); break;
+            case 2: K::template load_chunk<2>(sm, pn, x); break;
+            default: K::template load_chunk<3>(sm, pn, x); break;
+            }
+            cur = k;
+        }
+        wht_regs<RB>(x, d.r0lo, d.r0hi);
+        if (d.ph)
+            K::apply_slot(x, sh, exact);
+        wht_regs<RB>(x, d.r1lo, d.r1hi);
+    }
+    if (cur != kio) {
+        __syncthreads();
+        const uint32_t pc = padidx<ES>(base_of(cur));
+        switch (cur) {
+        case 0: K::template store_chunk<0>(sm, pc, x); break;
+        case 1: K::template store_chunk<1>(sm, pc, x); break;
+        case 2: K::template store_chunk<2>(sm, pc, x); break;
+        default: K::template store_chunk<3>(sm, pc, x); break;
+        }
+        __syncthreads();
+        if (kio == 0)
+            K::template load_chunk<0>(sm, padidx<ES>(base_io), x);
+        else
+            K::template load_chunk<1>(sm, padidx<ES>(base_io), x);
+    }
+
+    // ---- store in the I/O layout
+    // (opaque copies: keeps the compiler from holding the 2^RB load addresses live
+    // across the whole pass)
+    asm volatile("mov.b64 %0, %0;" : "+l"(gthr));
+#pragma unroll
+    for (int b = 0; b < RB; b++)
+        asm volatile("mov.b64 %0, %0;" : "+l"(gst[b]));
+#pragma unroll
+    for (int j = 0; j < NR; j++) {
+        uint64_t gi = gthr;
+#pragma unroll
+        for (int b = 0; b < RB; b++)
+            if ((j >> b) & 1)
+                gi |= gst[b];
+        __stcs(psi + gi, x[j]);
+    }
+}
+
+} // namespace ts4
