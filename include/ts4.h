@@ -195,6 +195,28 @@ TS4_API double ts_step_bound(const ts_ctx *ctx);
  */
 TS4_API uint64_t ts_tile_global_index(int N, int c, int w, int h, uint64_t f, uint64_t e);
 
+/*
+ * Norm and <S^z_j> of a caller-owned device state, computed without allocating
+ * any device memory.  The paper has no counterpart: this entry point serves
+ * callers that cannot call cudaMalloc where they need these numbers -- code
+ * running while a stream is captured into a CUDA graph (allocation is not a
+ * capturable operation) and hosts whose device memory is owned by their own
+ * allocator.
+ *   psi_dev  2^N amplitudes of precision prec, device memory (read only).
+ *   out_dev  N + 1 doubles of device memory owned by the caller:
+ *            out[0] = sum_s |psi_s|^2, out[1 + j] = sum_s |psi_s|^2 (bit_j(s) - 1/2)
+ *            = <S^z_{j+1}>.
+ *   cuda_stream  stream to enqueue on (NULL = legacy default stream); no host
+ *            synchronisation.
+ * Scratch: a static device array of 1024 x 35 doubles (about 280 KB), held by
+ * every device that loads the library until exit.  Its device address is set up
+ * on the first call made with a device current; make that first call before any
+ * stream capture.  All calls share the array, so calls that overlap on the GPU
+ * race.  Errors: TS_ERR_ARG (N outside [1, 34], a NULL pointer, an unknown
+ * precision), TS_ERR_CUDA.
+ */
+TS4_API ts_status ts_reduce_sz_static(const void *psi_dev, int N, ts_prec prec, double *out_dev, void *cuda_stream);
+
 /* Number of CUDA kernels this context has launched so far. */
 TS4_API int64_t ts_kernel_launches(const ts_ctx *ctx);
 

@@ -529,7 +529,7 @@ __global__ void k_sum_overlap(const C *__restrict__ a, const C *__restrict__ b, 
 }
 
 // Final stage: out[k] = sum over nblk blocks of part[b * K + k], fixed order.
-__global__ void k_sum_final(const double *__restrict__ part, int nblk, int K, double *__restrict__ out)
+static __global__ void k_sum_final(const double *__restrict__ part, int nblk, int K, double *__restrict__ out)
 {
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         double s = 0.0;

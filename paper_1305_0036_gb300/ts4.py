@@ -46,6 +46,7 @@ SIGNATURES = {
     "ts_step_bound": (_D, [_P]),
     "ts_tile_global_index": (_U64, [_I, _I, _I, _I, _U64, _U64]),
     "ts_kernel_launches": (_I64, [_P]),
+    "ts_reduce_sz_static": (_I, [_P, _I, _I, _P, _P]),
     "ts_version": (ctypes.c_char_p, []),
 }
 
@@ -165,6 +166,11 @@ def ts_tile_global_index(N, c, w, h, f, e):
 
 def ts_kernel_launches(ctx):
     return int(_lib.ts_kernel_launches(ctx))
+
+
+def ts_reduce_sz_static(psi_ptr, N, prec, out_ptr, stream=None):
+    """Norm and <S^z_j> of a device state into a device buffer of N + 1 doubles, with no allocation."""
+    _check(_lib.ts_reduce_sz_static(psi_ptr, int(N), int(prec), out_ptr, stream))
 
 
 def ts_version():

@@ -1,0 +1,59 @@
+"""The allocation-free reduction entry point (ts_reduce_sz_static).
+
+It serves callers that cannot allocate device memory at the point of use (for
+example code running under CUDA stream capture, where cudaMalloc is not
+allowed, or hosts whose device memory is handed out by their own allocator):
+the caller passes a device state and a device output buffer, and the library's
+only scratch is a fixed static device array.  The test checks it, through the
+C ABI, against ts_observe on the same state, on two calls in a row (the second
+call reuses the static array left by the first).  It lives in a file that
+pytest collects last so that a run stopping at the first failure has already
+run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1305_0036_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec,N,tol", [("c64", 18, 1e-6), ("c128", 15, 1e-13), ("c64", 9, 1e-6)])
+def test_static_reduction_matches_ts_observe_twice(prec, N, tol):
+    import torch
+    from paper_1305_0036_gb300 import build
+    build.build()
+    from paper_1305_0036_gb300 import ts4
+
+    torch.cuda.set_device(0)
+    s = W.random_system(N, 500 + N)
+    ctx = ts4.Context.from_system(s, prec=prec)
+    ctx.set_state(W.haar_state(N, 600 + N))
+    ctx.step(0.05, 1)
+    ref_norm = ctx.norm()
+    ref_sz = ctx.sz()
+    out = torch.full((N + 1,), float("nan"), dtype=torch.float64, device="cuda")
+    stream = ctypes.c_void_p(ctx.stream.cuda_stream)
+    p = ts4.TS_C64 if prec == "c64" else ts4.TS_C128
+    for call in range(2):
+        out.fill_(float("nan"))
+        ts4.ts_reduce_sz_static(ctx.psi.data_ptr(), N, p, out.data_ptr(), stream)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert abs(got[0] - ref_norm) <= tol, (call, got[0], ref_norm)
+        np.testing.assert_allclose(got[1:], ref_sz, atol=tol)
+    ctx.close()
+
+
+def test_static_reduction_rejects_bad_arguments():
+    from paper_1305_0036_gb300 import build
+    build.build()
+    from paper_1305_0036_gb300 import ts4
+    with pytest.raises(ts4.TS4Error) as e:
+        ts4.ts_reduce_sz_static(None, 10, ts4.TS_C64, None)
+    assert e.value.status == ts4.TS_ERR_ARG
+    with pytest.raises(ts4.TS4Error) as e:
+        ts4.ts_reduce_sz_static(1 << 20, 35, ts4.TS_C64, 1 << 20)
+    assert e.value.status == ts4.TS_ERR_ARG
