@@ -274,7 +274,7 @@ def run_ours(args, ws, rank, local):
                 "pass_traffic_gbs": dram_gbs, "pass_traffic_frac": dram_gbs / peak},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "k_pass", "alg_bytes_per_launch": alg_bytes_launch,
+                     "kernel": "k_tile", "alg_bytes_per_launch": alg_bytes_launch,
                      "avg_launch_ms": avg_pass_ms},
         "e2e": {"value": e2e_value, "unit": "TS4 steps/s", "h2d_bytes_per_step": state_bytes / args.steps,
                 "d2h_bytes_per_step": 8 * (N + 1), "final_norm": norm},

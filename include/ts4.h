@@ -196,6 +196,20 @@ TS4_API double ts_step_bound(const ts_ctx *ctx);
 TS4_API uint64_t ts_tile_global_index(int N, int c, int w, int h, uint64_t f, uint64_t e);
 
 /*
+ * Autotuner (Sec. 3.4, last paragraph: the best rotation schedule depends on the
+ * system size, so the paper searched it by brute force and stored the winners in
+ * a file).  Times one TS4 step of length tau, reps times, on a scratch copy of the
+ * current state for every tile size and coalescing width this build provides,
+ * and selects the fastest for this context (ts_get_schedule reports it).  The
+ * state itself is not changed.  cache_path (may be NULL): a text file of lines
+ * "<gpu> <N> <prec> <tile_bits> <coalesce_bits> <ms_per_step>"; a matching
+ * line is used instead of searching (best_ms is then -1), and a new result is
+ * appended.  best_ms (may be NULL) receives the best time per step in ms.
+ * Errors: TS_ERR_ARG, TS_ERR_STATE (no state), TS_ERR_OOM, TS_ERR_CUDA.
+ */
+TS4_API ts_status ts_autotune(ts_ctx *ctx, double tau, int reps, const char *cache_path, double *best_ms);
+
+/*
  * Norm and <S^z_j> of a caller-owned device state, computed without allocating
  * any device memory.  The paper has no counterpart: this entry point serves
  * callers that cannot call cudaMalloc where they need these numbers -- code
@@ -216,6 +230,53 @@ TS4_API uint64_t ts_tile_global_index(int N, int c, int w, int h, uint64_t f, ui
  * precision), TS_ERR_CUDA.
  */
 TS4_API ts_status ts_reduce_sz_static(const void *psi_dev, int N, ts_prec prec, double *out_dev, void *cuda_stream);
+
+/* ------------------------------------------------------------------ batched ensemble
+ * Many independent states of several systems of uneven N advance together:
+ * system k has N[k] spins, couplings Jx[k], Jy[k], Jz[k] (N[k]*N[k], upper
+ * triangle), z-fields h[k] (or NULL) and nstates[k] states stored one after the
+ * other (nstates[k] x 2^N[k] amplitudes).  This is the ensemble use of the
+ * method for typical-state averages (App. A: random-phase states stand in for
+ * the infinite-temperature density matrix).  Every system uses the same tile
+ * size; at each pass index one kernel launch covers every state of every
+ * system, and a whole ts_batch_step is captured into one CUDA graph and
+ * replayed (the graph is rebuilt only when tau or nsteps change).
+ */
+typedef struct ts_batch ts_batch;
+
+/* Errors: TS_ERR_ARG (no systems, a NULL array, nstates < 1, a system smaller
+ * than the smallest tile this build provides), TS_ERR_OOM, TS_ERR_CUDA. */
+TS4_API ts_status ts_batch_create(ts_batch **out, int nsys, const int *N, const double *const *Jx,
+                                  const double *const *Jy, const double *const *Jz, const double *const *h,
+                                  const int *nstates, ts_prec prec, void *cuda_stream);
+
+/* Binds caller-owned device memory (>= nstates x 2^N amplitudes, 256-byte aligned) for system sys. */
+TS4_API ts_status ts_batch_bind_states(ts_batch *b, int sys, void *dev, size_t bytes);
+
+/* Copies nstates x 2^N amplitudes of system sys in (host memory if on_device == 0). */
+TS4_API ts_status ts_batch_set_states(ts_batch *b, int sys, const void *amps, int on_device);
+
+/* Copies the states of system sys out (host memory if on_device == 0). */
+TS4_API ts_status ts_batch_get_states(ts_batch *b, int sys, void *amps, int on_device);
+
+/* Tile bits and coalescing bits for every system (0 = default); the tile may not exceed the smallest N. */
+TS4_API ts_status ts_batch_set_schedule(ts_batch *b, int tile_bits, int coalesce_bits);
+
+/* nsteps TS4 steps of length tau for every state: one CUDA graph launch (Sec. 2). */
+TS4_API ts_status ts_batch_step(ts_batch *b, double tau, int64_t nsteps);
+
+/* TS_NORM (one double per state) or TS_SZ (N[k] doubles per state), systems in
+ * order, states in order; synchronises the stream. */
+TS4_API ts_status ts_batch_observe(ts_batch *b, int what, double *out);
+
+/* Kernels launched so far (graph nodes count one each). */
+TS4_API int64_t ts_batch_kernel_launches(const ts_batch *b);
+
+/* Text of the last error of b (never NULL). */
+TS4_API const char *ts_batch_last_error(const ts_batch *b);
+
+/* Frees everything the library allocated for the batch; NULL is accepted. */
+TS4_API ts_status ts_batch_destroy(ts_batch *b);
 
 /* Number of CUDA kernels this context has launched so far. */
 TS4_API int64_t ts_kernel_launches(const ts_ctx *ctx);

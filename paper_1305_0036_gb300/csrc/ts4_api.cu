@@ -61,7 +61,7 @@ struct HostPass {
     int slot = -1;      // slot index or -1
     int phase_k = 0;    // chunk of the step that applies the slot
     int tab = -1;
-    bool exact = false; // c64: per-amplitude factor through sincospif (large angles)
+    int ymode = 0;      // c64 per-amplitude factor: 0 |y| <= 0.05, 1 |y| <= 0.5, 2 sincospif
 };
 
 struct Schedule {
@@ -281,19 +281,26 @@ void build_tab(unsigned char *dst, const ts_ctx *ctx, int TB, const HostSlot &sl
 // Upper bound of |y_j| (radians) in the c64 per-amplitude factor of a slot on tile group g:
 // every per-thread coefficient is at most |t| (|h/2| + sum |J/4|) of its spin; RB of them
 // plus the in-chunk quadratic terms.
-double slot_y_bound(const ts_ctx *ctx, const HostSlot &sl, int RB)
+// Bound on |y_j|, the per-amplitude remainder of the slot angle in the tile kernel:
+// y_j collects the terms of t E_alpha that involve the RB register spins of the
+// step that applies the slot (tile bits W .. W + RB - 1 of group g), each with a
+// sign, so |y_j| <= |t| sum over those spins of (|hh_i| + sum_m |Jq_im|).
+double slot_y_bound(const ts_ctx *ctx, const HostSlot &sl, const Group &g, int TB, int RB, int phase_k)
 {
     const int N = ctx->N;
     const double *Jq = ctx->Jq.data() + (size_t)sl.alpha * N * N;
     const double *hh = ctx->hh.data() + (size_t)sl.alpha * N;
-    double bmax = 0.0;
-    for (int i = 0; i < N; i++) {
-        double b = std::fabs(hh[i]);
-        for (int j = 0; j < N; j++)
-            b += std::fabs(Jq[i * N + j]);
-        bmax = std::max(bmax, b);
+    const int W = std::min(phase_k * RB, TB - RB);
+    double bound = 0.0;
+    for (int b = 0; b < RB; b++) {
+        const int l = W + b;
+        const int i = l < g.h ? g.w + l : l - g.h;
+        double r = std::fabs(hh[i]);
+        for (int m = 0; m < N; m++)
+            r += std::fabs(Jq[i * N + m]);
+        bound += r;
     }
-    return std::fabs(sl.t) * bmax * RB * 2.0;
+    return std::fabs(sl.t) * bound;
 }
 
 // I/O layout of a group.  The 5 lanes must hold the globally lowest bits of the
@@ -664,7 +671,10 @@ ts_status prepare_fused(ts_ctx *ctx, Schedule &S)
         if (p.slot < 0)
             continue;
         const HostSlot &sl = S.slots[p.slot];
-        p.exact = ctx->prec == TS_C64 && slot_y_bound(ctx, sl, RB) > 0.5;
+        if (ctx->prec == TS_C64) {
+            const double yb = slot_y_bound(ctx, sl, S.groups[p.group], TB, RB, p.phase_k);
+            p.ymode = yb <= 0.05 ? 0 : (yb <= 0.5 ? 1 : 2);
+        }
         auto key = std::make_tuple(sl.t, sl.alpha, sl.pcq, p.group, p.phase_k);
         auto it = seen.find(key);
         if (it != seen.end()) {
@@ -705,7 +715,7 @@ ts_status run_fused(ts_ctx *ctx, void *buf, const Schedule &S)
         if (p.slot >= 0)
             a.slot = S.slots[p.slot].dev();
         a.tab = p.tab < 0 ? 0 : p.tab;
-        a.exact_sincos = p.exact ? 1 : 0;
+        a.exact_sincos = p.ymode;
         a.io = S.io[p.group];
         a.ham = hd;
         const uint64_t nblk = UINT64_C(1) << (ctx->N - (g.c + g.h));
@@ -1217,6 +1227,533 @@ double ts_step_bound(const ts_ctx *ctx)
             mx = hs;
     }
     return mx > 0.0 ? 1.0 / std::sqrt(mx) : INFINITY;
+}
+
+} // extern "C"
+
+// ================================================================== batched ensemble
+//
+// Many states of several systems (uneven N) advance together: at every pass
+// index one k_tile_batch launch covers every state of every system, and the
+// whole ts_batch_step is captured into one CUDA graph and replayed.
+
+struct ts_batch {
+    int nsys = 0;
+    ts_prec prec = TS_C64;
+    cudaStream_t stream = nullptr;       // the caller's stream: graphs are launched here
+    cudaStream_t cap = nullptr;          // private stream used only to capture the graph
+    int TB = 0, cbits = 0;
+    std::vector<ts_ctx *> sys;       // couplings and schedule of each system
+    std::vector<int> nstates;
+    std::vector<Buf> psi;            // nstates x 2^N amplitudes per system
+    // device copies of the per-pass launch arguments
+    BatchSys *dsys = nullptr;
+    TileArgs *dargs = nullptr;
+    size_t dcap = 0;                 // entries
+    std::vector<uint64_t> blocks;    // blocks per pass index
+    // cached graph of the last (tau, nsteps)
+    cudaGraphExec_t gexec = nullptr;
+    double g_tau = 0.0;
+    int64_t g_n = -1;
+    int64_t g_nodes = 0;
+    double *dpart = nullptr;
+    size_t part_cap = 0;
+    double *hout = nullptr;
+    std::string err;
+    int64_t launches = 0;
+};
+
+namespace {
+
+ts_status bfail(ts_batch *b, ts_status st, const std::string &msg)
+{
+    if (b)
+        b->err = msg;
+    return st;
+}
+
+#define TS_BCUDA(b, call)                                                                         \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return bfail((b), e_ == cudaErrorMemoryAllocation ? TS_ERR_OOM : TS_ERR_CUDA,         \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+    } while (0)
+
+size_t batch_state_bytes(const ts_batch *b, int s)
+{
+    return (size_t)b->nstates[s] * state_bytes(b->sys[s]);
+}
+
+template <typename R, int TB, int RB>
+cudaError_t launch_batch_t(cudaStream_t st, const BatchSys *sys, const TileArgs *args, int nsys, uint64_t nblk)
+{
+    using K = TileKernel<R, TB, RB>;
+    constexpr size_t smem = sizeof(typename CT<R>::T) * K::SMEM_ELEMS;
+    k_tile_batch<R, TB, RB><<<(unsigned)nblk, K::NT, smem, st>>>(sys, args, nsys);
+    return cudaGetLastError();
+}
+
+template <typename R, int TB, int RB> cudaError_t batch_attr_t()
+{
+    using K = TileKernel<R, TB, RB>;
+    constexpr size_t smem = sizeof(typename CT<R>::T) * K::SMEM_ELEMS;
+    return cudaFuncSetAttribute(k_tile_batch<R, TB, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_batch(const ts_batch *b, const BatchSys *sys, const TileArgs *args, uint64_t nblk, bool attr)
+{
+    if (b->prec == TS_C64) {
+        switch (b->TB) {
+        case 12: return attr ? batch_attr_t<float, 12, 5>() : launch_batch_t<float, 12, 5>(b->stream, sys, args, b->nsys, nblk);
+        case 13: return attr ? batch_attr_t<float, 13, 5>() : launch_batch_t<float, 13, 5>(b->stream, sys, args, b->nsys, nblk);
+        default: return attr ? batch_attr_t<float, 14, 5>() : launch_batch_t<float, 14, 5>(b->stream, sys, args, b->nsys, nblk);
+        }
+    }
+    switch (b->TB) {
+    case 11: return attr ? batch_attr_t<double, 11, 4>() : launch_batch_t<double, 11, 4>(b->stream, sys, args, b->nsys, nblk);
+    case 12: return attr ? batch_attr_t<double, 12, 4>() : launch_batch_t<double, 12, 4>(b->stream, sys, args, b->nsys, nblk);
+    default: return attr ? batch_attr_t<double, 13, 4>() : launch_batch_t<double, 13, 4>(b->stream, sys, args, b->nsys, nblk);
+    }
+}
+
+void batch_drop_graph(ts_batch *b)
+{
+    if (b->gexec)
+        cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->g_n = -1;
+}
+
+// Builds every system's schedule for U4(tau)^n, the per-pass launch arguments, and
+// captures the launches into a CUDA graph.
+ts_status batch_prepare(ts_batch *b, double tau, int64_t n)
+{
+    batch_drop_graph(b);
+    size_t maxp = 0;
+    for (int s = 0; s < b->nsys; s++) {
+        ts_ctx *c = b->sys[s];
+        c->TB = b->TB;
+        c->cbits = b->cbits;
+        c->kernel = TS_KERNEL_FUSED;
+        reset_schedule(c->sched, b->stream);
+        c->sched.slots = make_slots(c->N, 4, tau, n);
+        ts_status st = prepare_fused(c, c->sched);
+        if (st)
+            return bfail(b, st, std::string("system schedule: ") + c->err);
+        maxp = std::max(maxp, c->sched.passes.size());
+    }
+    const size_t need = maxp * (size_t)b->nsys;
+    if (need > b->dcap) {
+        if (b->dsys)
+            cudaFree(b->dsys);
+        if (b->dargs)
+            cudaFree(b->dargs);
+        b->dsys = nullptr;
+        b->dargs = nullptr;
+        b->dcap = 0;
+        TS_BCUDA(b, cudaMalloc(&b->dsys, need * sizeof(BatchSys)));
+        TS_BCUDA(b, cudaMalloc(&b->dargs, need * sizeof(TileArgs)));
+        b->dcap = need;
+    }
+    std::vector<BatchSys> hs(need);
+    std::vector<TileArgs> ha(need);
+    b->blocks.assign(maxp, 0);
+    for (size_t p = 0; p < maxp; p++) {
+        uint32_t start = 0;
+        for (int s = 0; s < b->nsys; s++) {
+            ts_ctx *c = b->sys[s];
+            const Schedule &S = c->sched;
+            BatchSys &bs = hs[p * b->nsys + s];
+            TileArgs &a = ha[p * b->nsys + s];
+            std::memset(&bs, 0, sizeof(bs));
+            std::memset(&a, 0, sizeof(a));
+            bs.psi = b->psi[s].p;
+            bs.tabs = S.dtab;
+            bs.n = c->N;
+            bs.tile_shift = c->N - b->TB;
+            bs.block_start = start;
+            bs.active = p < S.passes.size();
+            if (!bs.active)
+                continue;
+            const HostPass &hp = S.passes[p];
+            const Group &g = S.groups[hp.group];
+            a.c = g.c;
+            a.w = g.w;
+            a.h = g.h;
+            a.nsteps = hp.nsteps;
+            std::memcpy(a.steps, hp.steps, sizeof(hp.steps));
+            a.has_slot = hp.slot >= 0;
+            if (hp.slot >= 0)
+                a.slot = S.slots[hp.slot].dev();
+            a.tab = hp.tab < 0 ? 0 : hp.tab;
+            a.exact_sincos = hp.ymode;
+            a.io = S.io[hp.group];
+            a.ham = ham_dev(c);
+            start += (uint32_t)((uint64_t)b->nstates[s] << bs.tile_shift);
+        }
+        b->blocks[p] = start;
+    }
+    TS_BCUDA(b, cudaMemcpyAsync(b->dsys, hs.data(), need * sizeof(BatchSys), cudaMemcpyHostToDevice, b->stream));
+    TS_BCUDA(b, cudaMemcpyAsync(b->dargs, ha.data(), need * sizeof(TileArgs), cudaMemcpyHostToDevice, b->stream));
+    TS_BCUDA(b, cudaStreamSynchronize(b->stream));
+    TS_BCUDA(b, launch_batch(b, nullptr, nullptr, 0, true));
+    // capture the whole evolution into one graph
+    cudaGraph_t graph = nullptr;
+    // (the legacy default stream cannot be captured: record on a private stream)
+    TS_BCUDA(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaSuccess;
+    const cudaStream_t user = b->stream;
+    b->stream = b->cap;
+    for (size_t p = 0; p < maxp && ce == cudaSuccess; p++)
+        if (b->blocks[p])
+            ce = launch_batch(b, b->dsys + p * b->nsys, b->dargs + p * b->nsys, b->blocks[p], false);
+    b->stream = user;
+    cudaError_t ee = cudaStreamEndCapture(b->cap, &graph);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        return bfail(b, TS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    size_t nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nodes);
+    cudaError_t ie = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        b->gexec = nullptr;
+        return bfail(b, TS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    }
+    b->g_tau = tau;
+    b->g_n = n;
+    b->g_nodes = (int64_t)nodes;
+    return TS_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+ts_status ts_batch_create(ts_batch **out, int nsys, const int *N, const double *const *Jx, const double *const *Jy,
+                          const double *const *Jz, const double *const *h, const int *nstates, ts_prec prec,
+                          void *cuda_stream)
+{
+    if (!out)
+        return TS_ERR_ARG;
+    *out = nullptr;
+    if (nsys < 1 || !N || !Jx || !Jy || !Jz || !nstates || (prec != TS_C64 && prec != TS_C128))
+        return TS_ERR_ARG;
+    ts_batch *b = new (std::nothrow) ts_batch();
+    if (!b)
+        return TS_ERR_OOM;
+    b->nsys = nsys;
+    b->prec = prec;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->TB = default_tile(prec);
+    b->cbits = default_cbits(prec);
+    int nmin = 64;
+    for (int s = 0; s < nsys; s++) {
+        if (nstates[s] < 1) {
+            ts_batch_destroy(b);
+            return TS_ERR_ARG;
+        }
+        ts_ctx *c = nullptr;
+        ts_status st = ts_create(&c, N[s], Jx[s], Jy[s], Jz[s], h ? h[s] : nullptr, prec, cuda_stream);
+        if (st) {
+            ts_batch_destroy(b);
+            return st;
+        }
+        b->sys.push_back(c);
+        b->nstates.push_back(nstates[s]);
+        b->psi.push_back(Buf());
+        nmin = std::min(nmin, N[s]);
+    }
+    if (!tile_supported(prec, b->TB) || nmin < b->TB) {
+        // the smallest system sets the largest usable tile
+        int tb = std::min(b->TB, nmin);
+        if (!tile_supported(prec, tb)) {
+            ts_batch_destroy(b);
+            return TS_ERR_ARG;
+        }
+        b->TB = tb;
+    }
+    TS_BCUDA(b, cudaMallocHost(&b->hout, (kMaxN + 8) * sizeof(double)));
+    TS_BCUDA(b, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    *out = b;
+    return TS_OK;
+}
+
+ts_status ts_batch_bind_states(ts_batch *b, int sys, void *dev, size_t bytes)
+{
+    if (!b || sys < 0 || sys >= b->nsys || !dev)
+        return b ? bfail(b, TS_ERR_ARG, "ts_batch_bind_states: bad system or pointer") : TS_ERR_ARG;
+    if (bytes < batch_state_bytes(b, sys) || ((uintptr_t)dev & 255))
+        return bfail(b, TS_ERR_ARG, "ts_batch_bind_states: buffer too small or not 256-byte aligned");
+    free_buf(b->psi[sys]);
+    b->psi[sys].p = dev;
+    batch_drop_graph(b);
+    return TS_OK;
+}
+
+static ts_status batch_ensure(ts_batch *b, int s)
+{
+    if (b->psi[s].p)
+        return TS_OK;
+    cudaError_t e = cudaMalloc(&b->psi[s].p, batch_state_bytes(b, s));
+    if (e != cudaSuccess) {
+        b->psi[s].p = nullptr;
+        return bfail(b, TS_ERR_OOM, "ts_batch: state buffer allocation failed");
+    }
+    b->psi[s].own = true;
+    batch_drop_graph(b);
+    return TS_OK;
+}
+
+ts_status ts_batch_set_states(ts_batch *b, int sys, const void *amps, int on_device)
+{
+    if (!b || sys < 0 || sys >= b->nsys || !amps)
+        return b ? bfail(b, TS_ERR_ARG, "ts_batch_set_states: bad system or pointer") : TS_ERR_ARG;
+    ts_status st = batch_ensure(b, sys);
+    if (st)
+        return st;
+    TS_BCUDA(b, cudaMemcpyAsync(b->psi[sys].p, amps, batch_state_bytes(b, sys),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
+    if (!on_device)
+        TS_BCUDA(b, cudaStreamSynchronize(b->stream));
+    return TS_OK;
+}
+
+ts_status ts_batch_get_states(ts_batch *b, int sys, void *amps, int on_device)
+{
+    if (!b || sys < 0 || sys >= b->nsys || !amps || !b->psi[sys].p)
+        return b ? bfail(b, TS_ERR_ARG, "ts_batch_get_states: bad system, pointer or no state") : TS_ERR_ARG;
+    TS_BCUDA(b, cudaMemcpyAsync(amps, b->psi[sys].p, batch_state_bytes(b, sys),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
+    if (!on_device)
+        TS_BCUDA(b, cudaStreamSynchronize(b->stream));
+    return TS_OK;
+}
+
+ts_status ts_batch_set_schedule(ts_batch *b, int tile_bits, int coalesce_bits)
+{
+    if (!b)
+        return TS_ERR_ARG;
+    int nmin = 64;
+    for (auto *c : b->sys)
+        nmin = std::min(nmin, c->N);
+    const int tb = tile_bits ? tile_bits : std::min(default_tile(b->prec), nmin);
+    const int cb = coalesce_bits ? coalesce_bits : default_cbits(b->prec);
+    if (!tile_supported(b->prec, tb) || tb > nmin || cb < 1 || cb > tb - reg_bits(b->prec))
+        return bfail(b, TS_ERR_ARG, "ts_batch_set_schedule: tile not provided or larger than the smallest system");
+    b->TB = tb;
+    b->cbits = cb;
+    batch_drop_graph(b);
+    return TS_OK;
+}
+
+ts_status ts_batch_step(ts_batch *b, double tau, int64_t nsteps)
+{
+    if (!b)
+        return TS_ERR_ARG;
+    if (!std::isfinite(tau) || nsteps < 0)
+        return bfail(b, TS_ERR_ARG, "ts_batch_step: tau must be finite and nsteps >= 0");
+    for (int s = 0; s < b->nsys; s++)
+        if (!b->psi[s].p)
+            return bfail(b, TS_ERR_STATE, "ts_batch_step: a system has no states set");
+    if (nsteps == 0)
+        return TS_OK;
+    if (!b->gexec || b->g_tau != tau || b->g_n != nsteps) {
+        ts_status st = batch_prepare(b, tau, nsteps);
+        if (st)
+            return st;
+    }
+    TS_BCUDA(b, cudaGraphLaunch(b->gexec, b->stream));
+    b->launches += b->g_nodes;
+    return TS_OK;
+}
+
+ts_status ts_batch_observe(ts_batch *b, int what, double *out)
+{
+    if (!b || !out)
+        return b ? bfail(b, TS_ERR_ARG, "ts_batch_observe: NULL output") : TS_ERR_ARG;
+    if (what != TS_NORM && what != TS_SZ)
+        return bfail(b, TS_ERR_ARG, "ts_batch_observe: only TS_NORM and TS_SZ are batched");
+    size_t o = 0;
+    for (int s = 0; s < b->nsys; s++) {
+        ts_ctx *c = b->sys[s];
+        if (!b->psi[s].p)
+            return bfail(b, TS_ERR_STATE, "ts_batch_observe: a system has no states set");
+        const size_t sb = state_bytes(c);
+        for (int k = 0; k < b->nstates[s]; k++) {
+            std::vector<double> v(c->N + 1);
+            ts_status st = sum_sz(c, (const char *)b->psi[s].p + (size_t)k * sb, v.data());
+            if (st)
+                return bfail(b, st, c->err);
+            b->launches += 2;
+            if (what == TS_NORM)
+                out[o++] = v[0];
+            else
+                for (int j = 0; j < c->N; j++)
+                    out[o++] = v[1 + j] - 0.5 * v[0];
+        }
+    }
+    return TS_OK;
+}
+
+int64_t ts_batch_kernel_launches(const ts_batch *b) { return b ? b->launches : 0; }
+
+const char *ts_batch_last_error(const ts_batch *b) { return b ? b->err.c_str() : ""; }
+
+ts_status ts_batch_destroy(ts_batch *b)
+{
+    if (!b)
+        return TS_OK;
+    cudaStreamSynchronize(b->stream);
+    batch_drop_graph(b);
+    for (auto &p : b->psi)
+        free_buf(p);
+    for (auto *c : b->sys)
+        ts_destroy(c);
+    if (b->dsys)
+        cudaFree(b->dsys);
+    if (b->dargs)
+        cudaFree(b->dargs);
+    if (b->hout)
+        cudaFreeHost(b->hout);
+    if (b->cap)
+        cudaStreamDestroy(b->cap);
+    delete b;
+    return TS_OK;
+}
+
+} // extern "C"
+
+// ================================================================== autotuner
+//
+// Sec. 3.4 (last paragraph): no rotation schedule is best for every size, so the
+// paper searched them by brute force and stored the winners in a file.  Here the
+// search space is the tile size and the coalescing bits of the fused kernel.
+
+namespace {
+
+std::string device_name()
+{
+    int dev = 0;
+    cudaDeviceProp p;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&p, dev) != cudaSuccess)
+        return "unknown";
+    std::string n = p.name;
+    for (auto &ch : n)
+        if (ch == ' ')
+            ch = '_';
+    return n;
+}
+
+// Cache file lines: "<gpu> <N> <prec> <tile_bits> <coalesce_bits> <ms_per_step>"
+bool tune_lookup(const char *path, const std::string &gpu, int N, int prec, int *tb, int *cb)
+{
+    FILE *f = path ? std::fopen(path, "r") : nullptr;
+    if (!f)
+        return false;
+    char g[256];
+    int n, p, t, c;
+    double ms;
+    bool found = false;
+    while (std::fscanf(f, "%255s %d %d %d %d %lf", g, &n, &p, &t, &c, &ms) == 6)
+        if (gpu == g && n == N && p == prec) {
+            *tb = t;
+            *cb = c;
+            found = true;
+        }
+    std::fclose(f);
+    return found;
+}
+
+void tune_store(const char *path, const std::string &gpu, int N, int prec, int tb, int cb, double ms)
+{
+    FILE *f = path ? std::fopen(path, "a") : nullptr;
+    if (!f)
+        return;
+    std::fprintf(f, "%s %d %d %d %d %.6f\n", gpu.c_str(), N, prec, tb, cb, ms);
+    std::fclose(f);
+}
+
+} // namespace
+
+extern "C" {
+
+ts_status ts_autotune(ts_ctx *ctx, double tau, int reps, const char *cache_path, double *best_ms)
+{
+    if (!ctx || !std::isfinite(tau) || reps < 1)
+        return ctx ? fail(ctx, TS_ERR_ARG, "ts_autotune: tau must be finite and reps >= 1") : TS_ERR_ARG;
+    if (!ctx->psi.p)
+        return fail(ctx, TS_ERR_STATE, "ts_autotune: no state set");
+    const std::string gpu = device_name();
+    int tb = 0, cb = 0;
+    if (tune_lookup(cache_path, gpu, ctx->N, (int)ctx->prec, &tb, &cb) && tile_supported(ctx->prec, tb) &&
+        ctx->N >= tb) {
+        if (best_ms)
+            *best_ms = -1.0;
+        return ts_set_schedule(ctx, TS_KERNEL_FUSED, tb, cb);
+    }
+    ts_status st = ensure_buf(ctx, ctx->scratch, "autotune scratch buffer");
+    if (st)
+        return st;
+    const int keep_k = ctx->kernel, keep_tb = ctx->TB, keep_cb = ctx->cbits;
+    double best = 1e300;
+    int btb = keep_tb, bcb = keep_cb;
+    cudaEvent_t e0, e1;
+    TS_CUDA(ctx, cudaEventCreate(&e0));
+    TS_CUDA(ctx, cudaEventCreate(&e1));
+    const int tbs64[3] = {12, 13, 14}, tbs128[3] = {11, 12, 13};
+    for (int i = 0; i < 3 && !st; i++) {
+        const int t = ctx->prec == TS_C64 ? tbs64[i] : tbs128[i];
+        if (ctx->N < t)
+            continue;
+        for (int c = 1; c <= 4 && !st; c++) {
+            if (c > t - ctx->RB)
+                continue;
+            ctx->kernel = TS_KERNEL_FUSED;
+            ctx->TB = t;
+            ctx->cbits = c;
+            Schedule trial;
+            const std::vector<HostSlot> slots = make_slots(ctx->N, 4, tau, 1);
+            st = (ts_status)cudaMemcpyAsync(ctx->scratch.p, ctx->psi.p, state_bytes(ctx), cudaMemcpyDeviceToDevice,
+                                            ctx->stream);
+            if (st) {
+                st = TS_ERR_CUDA;
+                break;
+            }
+            st = run_slots(ctx, trial, ctx->scratch.p, 4, tau, 1, 0, slots);   // warm-up and schedule build
+            if (!st)
+                st = (ts_status)cudaEventRecord(e0, ctx->stream);
+            for (int r = 0; r < reps && !st; r++)
+                st = run_slots(ctx, trial, ctx->scratch.p, 4, tau, 1, 0, slots);
+            if (!st)
+                st = (ts_status)cudaEventRecord(e1, ctx->stream);
+            if (!st)
+                st = (ts_status)cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (!st && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms / reps < best) {
+                best = ms / reps;
+                btb = t;
+                bcb = c;
+            }
+            reset_schedule(trial, ctx->stream);
+            if (st && st != TS_ERR_CUDA && st != TS_ERR_OOM && st != TS_ERR_ARG)
+                st = TS_ERR_CUDA;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->kernel = keep_k;
+    ctx->TB = keep_tb;
+    ctx->cbits = keep_cb;
+    if (st)
+        return fail(ctx, st, "ts_autotune: a trial failed: " + ctx->err);
+    if (best_ms)
+        *best_ms = best;
+    tune_store(cache_path, gpu, ctx->N, (int)ctx->prec, btb, bcb, best);
+    return ts_set_schedule(ctx, TS_KERNEL_FUSED, btb, bcb);
 }
 
 } // extern "C"

@@ -56,17 +56,25 @@ __global__ void k_slot_basic(typename CT<R>::T *__restrict__ psi, uint64_t dim, 
     using C = typename CT<R>::T;
     const double *Jq = ham.Jq + (size_t)sl.alpha * ham.N * ham.N;
     const double *hh = ham.hh + (size_t)sl.alpha * ham.N;
-    const R scale = (R)ldexp(sl.mag, -sl.scale_exp);
+    const double scale = ldexp(sl.mag, -sl.scale_exp);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < dim; s += stride) {
         double th = sl.th0;
         if (sl.t != 0.0)
             th += sl.t * energy_bits(s, Jq, hh, ham.N);
-        C f = cexpm_pi((R)halfturns_2pi(th));
+        // the factor is formed and applied in FP64 for both precisions: a complex64 factor
+        // near 1 would be off the unit circle by a rounding error that depends only on the
+        // energy level, which acts on the norm coherently over many steps
+        double2 f = cexpm_pi(halfturns_2pi(th));
         f.x *= scale;
         f.y *= scale;
         f = cmul_ipow(f, sl.pcq * __popcll(s));
-        psi[s] = cmul(psi[s], f);
+        const C x = psi[s];
+        const double2 y = cmul(make_double2((double)x.x, (double)x.y), f);
+        C r;
+        r.x = (R)y.x;
+        r.y = (R)y.y;
+        psi[s] = r;
     }
 }
 

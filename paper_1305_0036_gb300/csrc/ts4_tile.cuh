@@ -84,7 +84,7 @@ struct TileArgs {
     Slot slot;
     int has_slot;
     int tab;
-    int exact_sincos;   // c64: use sincospif for the per-amplitude factor (|y| may exceed 0.5)
+    int exact_sincos;   // c64 per-amplitude factor: 0 if |y| <= 0.05, 1 if |y| <= 0.5, 2 otherwise (sincospif)
     IOLayout io;
     HamDev ham;
 };
@@ -95,10 +95,10 @@ struct TileArgs {
 template <typename R, int TB, int RB> using TileTab = PassTab<R, TB, RB>;
 
 struct SlotThreadC64 {
-    float2 T;
+    float2 R[6];      // T i^{pcq p}, p = popcount of the register index
     float Lo[8];
     float Hi[4];
-    int pcq;
+    float kT;         // |T (1 + kT)| = |scale| to ~1e-14: the FP32 magnitude error of T, removed
 };
 
 struct SlotThreadC128 {
@@ -144,15 +144,6 @@ __device__ __forceinline__ float2 cexpm_small(float y)
 
 __host__ __device__ constexpr int popc_c(int v) { return v ? (v & 1) + popc_c(v >> 1) : 0; }
 
-// a * i^k for a run-time k, without branches: swap for odd k, negate for k = 2, 3
-__device__ __forceinline__ float2 rot_ipow(float2 a, int k)
-{
-    const bool odd = k & 1;
-    const float sg = (k & 2) ? -1.0f : 1.0f;
-    const float rx = odd ? -a.y : a.x;
-    const float ry = odd ? a.x : a.y;
-    return make_float2(sg * rx, sg * ry);
-}
 
 // c64 slot, one factor per amplitude:
 //   F(j) = T_thread * e^{-i y_j} * i^{pcq popcount(j)},
@@ -161,22 +152,25 @@ __device__ __forceinline__ float2 rot_ipow(float2 a, int k)
 // Rounding happens per amplitude (no table of rounded factors shared by many
 // amplitudes), so the errors do not build up coherently over the steps.
 
-// Per-thread part (one copy for every layout: W is a run-time value).
-template <int TB, int RB>
-__device__ __forceinline__ void slot_thread_c64(SlotThreadC64 &o, uint32_t base, int W,
-                                             const TileShared<float, TB, RB> &sh, int pcq, float scale)
+// Per-thread part, for the register window W of the layout that applies the slot
+// (compile-time W: only the thread's own bits enter the unrolled sums).
+template <int TB, int RB, int W>
+__device__ __forceinline__ void slot_thread_c64_w(SlotThreadC64 &o, uint32_t base, const TileShared<float, TB, RB> &sh,
+                                                  int pcq, float scale, float srel)
 {
+    constexpr uint32_t chunk = ((1u << RB) - 1u) << W;
     float sacc = 0.0f;
     float cb[RB];
 #pragma unroll
     for (int b = 0; b < RB; b++)
         cb[b] = sh.g[W + b];
-    const uint32_t chunk = ((1u << RB) - 1u) << W;
+#pragma unroll
     for (int m = 0; m < TB; m++) {
         if ((chunk >> m) & 1u)
             continue;
         const float sm = ((base >> m) & 1u) ? 1.0f : -1.0f;
         sacc = fmaf(sm, sh.g[m], sacc);
+#pragma unroll
         for (int l = m + 1; l < TB; l++) {
             if ((chunk >> l) & 1u)
                 continue;
@@ -194,7 +188,19 @@ __device__ __forceinline__ void slot_thread_c64(SlotThreadC64 &o, uint32_t base,
     float sn, cs;
     sincospif(r, &sn, &cs);
     const int kt = (pcq * (sh.pcF + __popc(base)) - (int)q) & 3;
-    o.T = cmul_ipow(make_float2(cs * scale, -sn * scale), kt);
+    const float2 T = cmul_ipow(make_float2(cs * scale, -sn * scale), kt);
+    // magnitude error d = cs^2 + sn^2 - 1 of the FP32 pair, to ~1e-14 (exact products by FMA;
+    // cs^2 in [1/2, 1] so cs^2 - 1 is exact); (1 - d/2) restores unit magnitude
+    {
+        const float p1 = cs * cs, e1 = fmaf(cs, cs, -p1);
+        const float p2 = sn * sn, e2 = fmaf(sn, sn, -p2);
+        const float d = ((p1 - 1.0f) + p2) + (e1 + e2);
+        o.kT = fmaf(-0.5f, d, srel);
+    }
+    // the factor of register j is T i^{pcq popcount(j)} e^{-i y_j}: keep T i^{pcq p}, p = 0..5
+#pragma unroll
+    for (int p = 0; p <= RB; p++)
+        o.R[p] = cmul_ipow(T, (pcq * p) & 3);
     o.Lo[0] = 0.0f;
 #pragma unroll
     for (int b = 0; b < 3; b++)
@@ -208,28 +214,95 @@ __device__ __forceinline__ void slot_thread_c64(SlotThreadC64 &o, uint32_t base,
     o.Hi[1] = cb[3] - cb[4];
     o.Hi[2] = -cb[3] + cb[4];
     o.Hi[3] = cb[3] + cb[4];
-    o.pcq = pcq;
 }
 
-template <int RB>
-__device__ __forceinline__ void slot_c64(float2 (&x)[1 << RB], const SlotThreadC64 &o, const float2 *__restrict__ Q,
-                                         bool exact)
+template <int TB, int RB>
+__device__ __forceinline__ void slot_thread_c64(SlotThreadC64 &o, uint32_t base, int k,
+                                                const TileShared<float, TB, RB> &sh, int pcq, float scale,
+                                                float srel)
 {
-    const int pcq = o.pcq;
+    switch (k) {
+    case 0: slot_thread_c64_w<TB, RB, chunk_w<TB, RB>(0)>(o, base, sh, pcq, scale, srel); break;
+    case 1: slot_thread_c64_w<TB, RB, chunk_w<TB, RB>(1)>(o, base, sh, pcq, scale, srel); break;
+    case 2: slot_thread_c64_w<TB, RB, chunk_w<TB, RB>(2)>(o, base, sh, pcq, scale, srel); break;
+    default: slot_thread_c64_w<TB, RB, chunk_w<TB, RB>(3)>(o, base, sh, pcq, scale, srel); break;
+    }
+}
+
+// e^{-iy} = (1 + c) - i s with s = sin y and c = cos y - 1, |(1 + c, s)| = 1 to ~1e-14:
+// mode 0 (|y| <= 0.05): s from its Taylor series, c = -(1 - sqrt(1 - s^2)) from the
+//   binomial series in u = s^2 (truncation < 2e-12), so that the pair stays on the unit circle;
+// mode 1 (|y| <= 0.5): Taylor series of both, then the magnitude error d = 2c + c^2 + s^2
+//   is removed to first order;
+// mode 2 (any y): CUDA's sincospif, then the same correction.
+template <int MODE> __device__ __forceinline__ void unit_factor(float y, float &c, float &s)
+{
+    if constexpr (MODE == 0) {
+        const float y2 = y * y;
+        float ps = fmaf(y2, 1.0f / 120.0f, -1.0f / 6.0f);
+        ps = fmaf(y2, ps, 1.0f);
+        s = y * ps;
+        const float u = s * s;
+        float pc = fmaf(u, 1.0f / 16.0f, 1.0f / 8.0f);
+        pc = fmaf(u, pc, 0.5f);
+        c = -u * pc;
+    } else {
+        if constexpr (MODE == 1) {
+            const float y2 = y * y;
+            float pc = fmaf(y2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+            pc = fmaf(y2, pc, -1.0f / 720.0f);
+            pc = fmaf(y2, pc, 1.0f / 24.0f);
+            pc = fmaf(y2, pc, -0.5f);
+            c = y2 * pc;
+            float ps = fmaf(y2, -1.0f / 39916800.0f, 1.0f / 362880.0f);
+            ps = fmaf(y2, ps, -1.0f / 5040.0f);
+            ps = fmaf(y2, ps, 1.0f / 120.0f);
+            ps = fmaf(y2, ps, -1.0f / 6.0f);
+            ps = fmaf(y2, ps, 1.0f);
+            s = y * ps;
+        } else {
+            float cc;
+            sincospif(y * 0.31830988618379067f, &s, &cc);
+            c = cc - 1.0f;
+        }
+        const float d = fmaf(s, s, fmaf(c, c, 2.0f * c));
+        c = fmaf(-0.5f, d, c);
+        s = fmaf(-0.5f * d, s, s);
+    }
+}
+
+// Per-amplitude factors: x_j <- (x_j R[popcount j]) ((1 + c_j) - i s_j).  Every factor has
+// unit magnitude to ~1e-14 times the exact scale; the two FP32 roundings left are those of
+// products with x_j, which change from step to step, so they do not build up coherently.
+template <int RB, int MODE>
+__device__ __forceinline__ void slot_c64_apply(float2 (&x)[1 << RB], const SlotThreadC64 &o,
+                                               const float2 *__restrict__ Q)
+{
+    const float kT = o.kT;
 #pragma unroll
     for (int j = 0; j < (1 << RB); j++) {
         const float2 qv = Q[j];
         const float y = ((o.Lo[j & 7] + o.Hi[j >> 3]) + qv.x) + qv.y;
-        float2 E;
-        if (!exact) {
-            E = cexpm_small(y);
-        } else {
-            float s2, c2;
-            sincospif(y * 0.31830988618379067f, &s2, &c2);
-            E = make_float2(c2, -s2);
-        }
-        x[j] = cmul(x[j], cmul(o.T, rot_ipow(E, (pcq * popc_c(j)) & 3)));
+        float c, s;
+        unit_factor<MODE>(y, c, s);
+        // fold T's magnitude correction: (1 + c)(1 + kT) = 1 + (c + kT + c kT)
+        const float ct = fmaf(c, kT, c + kT);
+        const float st = fmaf(s, kT, s);
+        const float2 x1 = cmul(x[j], o.R[popc_c(j)]);
+        x[j] = make_float2(fmaf(x1.x, ct, fmaf(x1.y, st, x1.x)), fmaf(x1.y, ct, fmaf(-x1.x, st, x1.y)));
     }
+}
+
+template <int RB>
+__device__ __forceinline__ void slot_c64(float2 (&x)[1 << RB], const SlotThreadC64 &o, const float2 *__restrict__ Q,
+                                         int mode)
+{
+    if (mode == 0)
+        slot_c64_apply<RB, 0>(x, o, Q);
+    else if (mode == 1)
+        slot_c64_apply<RB, 1>(x, o, Q);
+    else
+        slot_c64_apply<RB, 2>(x, o, Q);
 }
 
 // c128 slot: per-thread factors (errors ~1e-16; table of the in-chunk terms).
@@ -324,19 +397,19 @@ template <typename R, int TB, int RB> struct TileKernel {
             x[j] = sm[pbase + padidx<ES>((uint32_t)j << W)];
     }
 
-    static __device__ __forceinline__ void apply_slot(C (&x)[NR], const TileShared<R, TB, RB> &sh, bool exact)
+    static __device__ __forceinline__ void apply_slot(C (&x)[NR], const TileShared<R, TB, RB> &sh, int mode)
     {
         if constexpr (sizeof(R) == 4)
-            slot_c64<RB>(x, sh.th_f[threadIdx.x], sh.Q, exact);
+            slot_c64<RB>(x, sh.th_f[threadIdx.x], sh.Q, mode);
         else
             slot_c128(x, sh.th_f[threadIdx.x], sh.Q);
     }
 };
 
+// One tile f of the state psi through the pass described by a.
 template <typename R, int TB, int RB>
-__global__ void __launch_bounds__(1 << (TB - RB), (TB - RB <= 8) ? 2 : 1)
-k_tile(typename CT<R>::T *__restrict__ psi, const __grid_constant__ TileArgs a,
-       const TileTab<R, TB, RB> *__restrict__ tabs)
+__device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, const TileArgs &a,
+                                          const TileTab<R, TB, RB> *__restrict__ tabs, uint64_t f)
 {
     using K = TileKernel<R, TB, RB>;
     using C = typename CT<R>::T;
@@ -348,7 +421,6 @@ k_tile(typename CT<R>::T *__restrict__ psi, const __grid_constant__ TileArgs a,
     __shared__ TileShared<R, TB, RB> sh;
 
     const uint32_t tid = threadIdx.x;
-    const uint64_t f = blockIdx.x;
     const int c = a.c, w = a.w, h = a.h;
     const uint64_t gbase = tile_global_index(c, w, h, f, 0);
 
@@ -388,7 +460,8 @@ k_tile(typename CT<R>::T *__restrict__ psi, const __grid_constant__ TileArgs a,
     // ---- per-block part of the slot, FP64
     int pcq = 0;
     R scale = R(1);
-    const bool exact = a.exact_sincos != 0;
+    float srel = 0.0f;                 // exact scale / rounded scale - 1 (c64: sqrt 1/2 is not exact)
+    const int mode = a.exact_sincos;   // c64 per-amplitude factor: 0 tiny |y|, 1 small |y|, 2 any
     if (a.has_slot) {
         const int N = a.ham.N;
         const int al = a.slot.alpha;
@@ -396,7 +469,9 @@ k_tile(typename CT<R>::T *__restrict__ psi, const __grid_constant__ TileArgs a,
         const double *Jq = a.ham.Jq + (size_t)al * N * N;
         const double *hh = a.ham.hh + (size_t)al * N;
         pcq = a.slot.pcq;
-        scale = (R)ldexp(a.slot.mag, -a.slot.scale_exp);
+        const double sx = ldexp(a.slot.mag, -a.slot.scale_exp);
+        scale = (R)sx;
+        srel = (float)(sx / (double)scale - 1.0);
         // g in radians (c64) or half-turns (c128)
         const double gunit = (sizeof(R) == 4) ? 1.0 : 0.31830988618379067153776752674503;
         if (tid < TB) {
@@ -444,7 +519,7 @@ k_tile(typename CT<R>::T *__restrict__ psi, const __grid_constant__ TileArgs a,
             if (a.steps[s].ph)
                 kph = a.steps[s].k;
         if constexpr (sizeof(R) == 4)
-            slot_thread_c64<TB, RB>(sh.th_f[tid], base_of(kph), chunk_w<TB, RB>(kph), sh, pcq, (float)scale);
+            slot_thread_c64<TB, RB>(sh.th_f[tid], base_of(kph), kph, sh, pcq, (float)scale, srel);
         else
             slot_thread_c128<TB, RB>(sh.th_f[tid], base_of(kph), chunk_w<TB, RB>(kph), sh, pcq, (double)scale);
     }
@@ -475,7 +550,7 @@ k_tile(typename CT<R>::T *__restrict__ psi, const __grid_constant__ TileArgs a,
         }
         wht_regs<RB>(x, d.r0lo, d.r0hi);
         if (d.ph)
-            K::apply_slot(x, sh, exact);
+            K::apply_slot(x, sh, mode);
         wht_regs<RB>(x, d.r1lo, d.r1hi);
     }
     if (cur != kio) {
@@ -510,6 +585,44 @@ k_tile(typename CT<R>::T *__restrict__ psi, const __grid_constant__ TileArgs a,
                 gi |= gst[b];
         __stcs(psi + gi, x[j]);
     }
+}
+
+template <typename R, int TB, int RB>
+__global__ void __launch_bounds__(1 << (TB - RB), (TB - RB <= 8) ? 2 : 1)
+k_tile(typename CT<R>::T *__restrict__ psi, const __grid_constant__ TileArgs a,
+       const TileTab<R, TB, RB> *__restrict__ tabs)
+{
+    tile_pass<R, TB, RB>(psi, a, tabs, blockIdx.x);
+}
+
+// Ensemble pass: every state of every system of a batch through its own pass
+// (one system's arguments per entry of `args`).  Blocks are laid out system by
+// system, state by state, tile by tile: block_start[s] is the first block of
+// system s, and system s has 2^tile_shift[s] tiles per state of 2^n[s] amplitudes.
+struct BatchSys {
+    void *psi;           // nstates x 2^n amplitudes
+    const void *tabs;    // this system's per-slot tables
+    int n;
+    int tile_shift;      // log2 tiles per state
+    uint32_t block_start;
+    int active;          // 0: this system has no pass at this index
+};
+
+template <typename R, int TB, int RB>
+__global__ void __launch_bounds__(1 << (TB - RB), (TB - RB <= 8) ? 2 : 1)
+k_tile_batch(const BatchSys *__restrict__ sys, const TileArgs *__restrict__ args, int nsys)
+{
+    const uint32_t b = blockIdx.x;
+    int s = 0;
+    while (s + 1 < nsys && sys[s + 1].block_start <= b)
+        s++;
+    if (!sys[s].active)
+        return;
+    const uint32_t local = b - sys[s].block_start;
+    const uint32_t state = local >> sys[s].tile_shift;
+    const uint64_t f = local & ((1u << sys[s].tile_shift) - 1u);
+    typename CT<R>::T *psi = reinterpret_cast<typename CT<R>::T *>(sys[s].psi) + ((uint64_t)state << sys[s].n);
+    tile_pass<R, TB, RB>(psi, args[s], reinterpret_cast<const TileTab<R, TB, RB> *>(sys[s].tabs), f);
 }
 
 } // namespace ts4

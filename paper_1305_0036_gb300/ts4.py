@@ -47,6 +47,17 @@ SIGNATURES = {
     "ts_tile_global_index": (_U64, [_I, _I, _I, _I, _U64, _U64]),
     "ts_kernel_launches": (_I64, [_P]),
     "ts_reduce_sz_static": (_I, [_P, _I, _I, _P, _P]),
+    "ts_autotune": (_I, [_P, _D, _I, ctypes.c_char_p, _P]),
+    "ts_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, _P, _P, _P, _P, _P, _I, _P]),
+    "ts_batch_bind_states": (_I, [_P, _I, _P, _SZ]),
+    "ts_batch_set_states": (_I, [_P, _I, _P, _I]),
+    "ts_batch_get_states": (_I, [_P, _I, _P, _I]),
+    "ts_batch_set_schedule": (_I, [_P, _I, _I]),
+    "ts_batch_step": (_I, [_P, _D, _I64]),
+    "ts_batch_observe": (_I, [_P, _I, _P]),
+    "ts_batch_kernel_launches": (_I64, [_P]),
+    "ts_batch_last_error": (ctypes.c_char_p, [_P]),
+    "ts_batch_destroy": (_I, [_P]),
     "ts_version": (ctypes.c_char_p, []),
 }
 
@@ -177,6 +188,104 @@ def ts_version():
     return _lib.ts_version().decode()
 
 
+def _bcheck(st, b):
+    if st != TS_OK:
+        raise TS4Error(st, _lib.ts_batch_last_error(b).decode() if b else "")
+
+
+class Batch:
+    """An ensemble of states of several systems (uneven N) evolved together.
+
+    systems: list of objects with N, Jx, Jy, Jz, hz; nstates: states per system.
+    Device memory for the states comes from torch (one tensor per system).
+    """
+
+    def __init__(self, systems, nstates, prec="c64", stream=None, device=None):
+        import torch
+        self.torch = torch
+        self.systems = list(systems)
+        self.nstates = [int(k) for k in nstates]
+        self.prec = TS_C64 if prec in ("c64", TS_C64) else TS_C128
+        self.dtype = torch.complex64 if self.prec == TS_C64 else torch.complex128
+        self.device = torch.device(device or "cuda")
+        n = len(self.systems)
+        Ns = (ctypes.c_int * n)(*[s.N for s in self.systems])
+        self._keep = []
+        def arr(attr):
+            ptrs = []
+            for s in self.systems:
+                a = getattr(s, attr)
+                if a is None:
+                    ptrs.append(None)
+                    continue
+                a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+                self._keep.append(a)
+                ptrs.append(a.ctypes.data)
+            return (ctypes.c_void_p * n)(*ptrs)
+        Jx, Jy, Jz, hz = arr("Jx"), arr("Jy"), arr("Jz"), arr("hz")
+        ks = (ctypes.c_int * n)(*self.nstates)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            out = _P()
+            _check(_lib.ts_batch_create(ctypes.byref(out), n, ctypes.cast(Ns, _P), ctypes.cast(Jx, _P),
+                                        ctypes.cast(Jy, _P), ctypes.cast(Jz, _P), ctypes.cast(hz, _P),
+                                        ctypes.cast(ks, _P), self.prec, ctypes.c_void_p(self.stream.cuda_stream)))
+            self.b = out
+            self.states = [torch.empty((k, 1 << s.N), dtype=self.dtype, device=self.device)
+                           for s, k in zip(self.systems, self.nstates)]
+        for i, t in enumerate(self.states):
+            _bcheck(_lib.ts_batch_bind_states(self.b, i, t.data_ptr(), t.numel() * t.element_size()), self.b)
+
+    def set_states(self, i, amps):
+        """amps: (nstates_i, 2^N_i) numpy array or device tensor."""
+        if isinstance(amps, self.torch.Tensor) and amps.is_cuda:
+            a = amps.to(self.dtype).contiguous()
+            _bcheck(_lib.ts_batch_set_states(self.b, i, a.data_ptr(), 1), self.b)
+        else:
+            a = np.ascontiguousarray(np.asarray(amps), dtype=np.complex64 if self.prec == TS_C64 else np.complex128)
+            _bcheck(_lib.ts_batch_set_states(self.b, i, a.ctypes.data, 0), self.b)
+
+    def get_states(self, i):
+        a = np.empty((self.nstates[i], 1 << self.systems[i].N),
+                     dtype=np.complex64 if self.prec == TS_C64 else np.complex128)
+        _bcheck(_lib.ts_batch_get_states(self.b, i, a.ctypes.data, 0), self.b)
+        return a
+
+    def set_schedule(self, tile_bits=0, coalesce_bits=0):
+        _bcheck(_lib.ts_batch_set_schedule(self.b, int(tile_bits), int(coalesce_bits)), self.b)
+
+    def step(self, tau, nsteps=1):
+        _bcheck(_lib.ts_batch_step(self.b, float(tau), int(nsteps)), self.b)
+
+    def norms(self):
+        out = np.zeros(sum(self.nstates))
+        _bcheck(_lib.ts_batch_observe(self.b, TS_NORM, out.ctypes.data), self.b)
+        return out
+
+    def sz(self):
+        out = np.zeros(sum(k * s.N for s, k in zip(self.systems, self.nstates)))
+        _bcheck(_lib.ts_batch_observe(self.b, TS_SZ, out.ctypes.data), self.b)
+        res, o = [], 0
+        for s, k in zip(self.systems, self.nstates):
+            res.append(out[o:o + k * s.N].reshape(k, s.N))
+            o += k * s.N
+        return res
+
+    def launches(self):
+        return int(_lib.ts_batch_kernel_launches(self.b))
+
+    def close(self):
+        if getattr(self, "b", None):
+            _lib.ts_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------- convenience wrapper
 
 class Context:
@@ -274,6 +383,14 @@ class Context:
 
     def schedule(self):
         return ts_get_schedule(self.ctx)
+
+    def autotune(self, tau, reps=2, cache_path=None):
+        """Brute-force search of the tile shape (library side); returns the best ms per step."""
+        self._aux("scratch")
+        ms = ctypes.c_double(0.0)
+        _check(_lib.ts_autotune(self.ctx, float(tau), int(reps),
+                                cache_path.encode() if cache_path else None, ctypes.byref(ms)), self.ctx)
+        return ms.value
 
     def step_bound(self):
         return ts_step_bound(self.ctx)

@@ -1,0 +1,80 @@
+"""Batched ensemble (several systems of uneven N, many states each) against the
+oracle and against single-state runs of the same library."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1305_0036_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def ts4():
+    from paper_1305_0036_gb300 import build
+    build.build()
+    from paper_1305_0036_gb300 import ts4 as m
+    return m
+
+
+def _ham(s):
+    return oracle.Hamiltonian(s.N, s.Jx, s.Jy, s.Jz, hz=s.hz, hx=s.hx, hy=s.hy)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_small_batch_matches_oracle(ts4, prec):
+    systems = [W.xyz_chain(n, 1.0, 0.8, 0.5, seed=900 + n) for n in (12, 13, 15)]
+    nst = [3, 2, 2]
+    b = ts4.Batch(systems, nst, prec=prec)
+    b.set_schedule(12, 2)
+    init = []
+    for i, (s, k) in enumerate(zip(systems, nst)):
+        a = np.stack([W.haar_state(s.N, 1000 + 10 * i + j) for j in range(k)])
+        init.append(a)
+        b.set_states(i, a)
+    nsteps, tau = 3, 0.05
+    b.step(tau, nsteps)
+    for i, (s, k) in enumerate(zip(systems, nst)):
+        got = b.get_states(i).astype(np.complex128)
+        for j in range(k):
+            ref = oracle.ts4(init[i][j], _ham(s), tau, nsteps)
+            if prec == "c128":
+                assert np.abs(got[j] - ref).max() <= 1e-12
+            else:
+                assert np.linalg.norm(got[j] - ref) <= 20 * nsteps * (s.N + 8) * U32
+    norms = b.norms()
+    assert np.all(np.abs(norms - 1) <= (1e-12 if prec == "c128" else 1e-5))
+    # a second call replays the cached graph
+    b.step(tau, nsteps)
+    assert b.launches() > 0
+    b.close()
+
+
+def test_config4_ensemble_against_single_state_runs(ts4):
+    """256 Haar states (64 each at N = 16, 18, 20, 22), XYZ chains, tau = 0.02, 200 steps,
+    complex64, one graph launch; sampled states checked against single-state runs."""
+    cfg = W.config(3)
+    systems, k = cfg["systems"], cfg["states_per_system"]
+    b = ts4.Batch(systems, [k] * len(systems), prec="c64")
+    init = []
+    for i, s in enumerate(systems):
+        a = np.stack([W.haar_state(s.N, cfg["state_seed"] * 1000 + 100 * i + j, np.complex64) for j in range(k)])
+        init.append(a)
+        b.set_states(i, a)
+    b.step(cfg["tau"], cfg["nsteps"])
+    norms = b.norms()
+    assert np.all(np.abs(norms - 1) <= 1e-4), np.abs(norms - 1).max()
+    szs = b.sz()
+    for i, s in enumerate(systems):
+        got = b.get_states(i)
+        for j in (0, k - 1):
+            c = ts4.Context.from_system(s, prec="c64")
+            c.set_state(init[i][j])
+            c.step(cfg["tau"], cfg["nsteps"])
+            single = c.get_state()
+            np.testing.assert_allclose(c.sz(), szs[i][j], atol=1e-6)
+            c.close()
+            # same kernels, same arithmetic: identical up to launch-independent rounding
+            assert np.linalg.norm(got[j].astype(np.complex128) - single) <= 1e-5
+    b.close()
