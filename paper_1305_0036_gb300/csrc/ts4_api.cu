@@ -62,6 +62,7 @@ struct HostPass {
     int phase_k = 0;    // chunk of the step that applies the slot
     int tab = -1;
     int ymode = 0;      // c64 per-amplitude factor: 0 |y| <= 0.05, 1 |y| <= 0.5, 2 sincospif
+    size_t theta_off = 0; // first entry of this pass's frame-angle table in Schedule::dtheta
 };
 
 struct Schedule {
@@ -79,17 +80,23 @@ struct Schedule {
     size_t tab_size = 0;
     void *dtab = nullptr;                // device copy, owned by this schedule
     size_t dtab_cap = 0;
+    double *dtheta = nullptr;            // frame angles of every (slot, group), owned by this schedule
+    size_t dtheta_cap = 0;               // doubles
 };
 
 // Frees S's device tables once the stream's queued passes (which read them) are done.
 void release_tables(Schedule &S, cudaStream_t st)
 {
-    if (S.dtab) {
+    if (S.dtab || S.dtheta)
         cudaStreamSynchronize(st);
+    if (S.dtab)
         cudaFree(S.dtab);
-    }
+    if (S.dtheta)
+        cudaFree(S.dtheta);
     S.dtab = nullptr;
     S.dtab_cap = 0;
+    S.dtheta = nullptr;
+    S.dtheta_cap = 0;
 }
 
 // Drops the pass list and tables of S (keeps nothing cached).
@@ -231,8 +238,24 @@ void build_tab_t(unsigned char *dst, const ts_ctx *ctx, const HostSlot &sl, cons
             if (l != m)
                 A[l * TB + m] = sl.t * Jq[pos(l) * N + pos(m)];
     const bool f32 = sizeof(R) == 4;
+    const double unit = f32 ? 1.0 : 1.0 / M_PI;
     for (int k = 0; k < TB * TB; k++)
-        tb.A[k] = (R)(f32 ? A[k] : A[k] / M_PI);
+        tb.A[k] = (R)(A[k] * unit);
+    // fields on the tile spins from the spins outside the tile
+    const double *hh = ctx->hh.data() + (size_t)sl.alpha * N;
+    std::vector<int> fpos;
+    for (int i = 0; i < N; i++)
+        if (!in_tile(i, g.c, g.w, g.h))
+            fpos.push_back(i);
+    tb.nf = (int)fpos.size();
+    for (int m = 0; m < tb.nf; m++)
+        tb.fpos[m] = fpos[m];
+    for (int l = 0; l < TB; l++) {
+        const int i = pos(l);
+        tb.G0[l] = (R)(sl.t * hh[i] * unit);
+        for (int m = 0; m < tb.nf; m++)
+            tb.GF[l * kMaxFrame + m] = (R)(sl.t * Jq[i * N + fpos[m]] * unit);
+    }
     const int W = chunk_w<TB, RB>(phase_k);
     for (int j = 0; j < (1 << RB); j++) {
         double q = 0.0;
@@ -687,13 +710,55 @@ ts_status prepare_fused(ts_ctx *ctx, Schedule &S)
         S.tabs.resize((size_t)(idx + 1) * S.tab_size);
         build_tab(S.tabs.data() + (size_t)idx * S.tab_size, ctx, TB, sl, S.groups[p.group], p.phase_k);
     }
-    if (S.tabs.size() > S.dtab_cap) {
+    // frame angles: one table of 2^(N - tile bits) values per distinct (slot, group)
+    struct ThetaJob {
+        const HostSlot *sl;
+        int group;
+        size_t off;
+    };
+    std::vector<ThetaJob> jobs;
+    std::map<std::tuple<double, int, double, int>, size_t> seen_th;
+    size_t ntheta = 0;
+    for (auto &p : S.passes) {
+        if (p.slot < 0)
+            continue;
+        const HostSlot &sl = S.slots[p.slot];
+        auto key = std::make_tuple(sl.t, sl.alpha, sl.th0, p.group);
+        auto it = seen_th.find(key);
+        if (it != seen_th.end()) {
+            p.theta_off = it->second;
+            continue;
+        }
+        const Group &g = S.groups[p.group];
+        p.theta_off = ntheta;
+        seen_th[key] = ntheta;
+        jobs.push_back({&sl, p.group, ntheta});
+        ntheta += (size_t)1 << (ctx->N - (g.c + g.h));
+    }
+    if (S.tabs.size() > S.dtab_cap || ntheta > S.dtheta_cap) {
         release_tables(S, ctx->stream);
-        TS_CUDA(ctx, cudaMalloc(&S.dtab, S.tabs.size()));
-        S.dtab_cap = S.tabs.size();
+        if (!S.tabs.empty()) {
+            TS_CUDA(ctx, cudaMalloc(&S.dtab, S.tabs.size()));
+            S.dtab_cap = S.tabs.size();
+        }
+        if (ntheta) {
+            TS_CUDA(ctx, cudaMalloc(&S.dtheta, ntheta * sizeof(double)));
+            S.dtheta_cap = ntheta;
+        }
     }
     if (!S.tabs.empty())
         TS_CUDA(ctx, cudaMemcpyAsync(S.dtab, S.tabs.data(), S.tabs.size(), cudaMemcpyHostToDevice, ctx->stream));
+    for (const auto &j : jobs) {
+        const Group &g = S.groups[j.group];
+        const int N = ctx->N;
+        const uint64_t nframes = UINT64_C(1) << (N - (g.c + g.h));
+        const unsigned blocks = (unsigned)std::min<uint64_t>((nframes + 127) / 128, (uint64_t)ctx->sms * 8);
+        k_frame_theta<<<blocks, 128, 0, ctx->stream>>>(ctx->dJq + (size_t)j.sl->alpha * N * N,
+                                                       ctx->dhh + (size_t)j.sl->alpha * N, N, g.c, g.w, g.h,
+                                                       j.sl->t, j.sl->th0, nframes, S.dtheta + j.off);
+        ctx->launches++;
+        TS_CUDA(ctx, cudaGetLastError());
+    }
     // the host image must stay valid until the copy is done
     TS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return TS_OK;
@@ -718,6 +783,7 @@ ts_status run_fused(ts_ctx *ctx, void *buf, const Schedule &S)
         a.exact_sincos = p.ymode;
         a.io = S.io[p.group];
         a.ham = hd;
+        a.theta = p.slot >= 0 ? S.dtheta + p.theta_off : nullptr;
         const uint64_t nblk = UINT64_C(1) << (ctx->N - (g.c + g.h));
         cudaError_t e = launch_tile(ctx, ctx->TB, buf, a, S.dtab, nblk);
         ctx->launches++;
@@ -748,9 +814,13 @@ ts_status run_slots(ts_ctx *ctx, Schedule &S, void *buf, int order, double tau, 
             // keep the device table buffer for reuse, rebuild everything else
             void *keep = S.dtab;
             const size_t keep_cap = S.dtab_cap;
+            double *keep_th = S.dtheta;
+            const size_t keep_th_cap = S.dtheta_cap;
             S = Schedule();
             S.dtab = keep;
             S.dtab_cap = keep_cap;
+            S.dtheta = keep_th;
+            S.dtheta_cap = keep_th_cap;
             S.slots = slots;
             st = prepare_fused(ctx, S);
             if (st == TS_OK) {
@@ -1390,6 +1460,7 @@ ts_status batch_prepare(ts_batch *b, double tau, int64_t n)
             a.exact_sincos = hp.ymode;
             a.io = S.io[hp.group];
             a.ham = ham_dev(c);
+            a.theta = hp.slot >= 0 ? S.dtheta + hp.theta_off : nullptr;
             start += (uint32_t)((uint64_t)b->nstates[s] << bs.tile_shift);
         }
         b->blocks[p] = start;

@@ -3,11 +3,8 @@
 //   k_wht_bit     one butterfly per thread on one spin over the whole state
 //                 (the paper's "GPU-Basic" kernel, Sec. 3.3 first paragraph)
 //   k_slot_basic  one diagonal slot per element, E(s) from bit tests (Sec. 3.1)
-//   k_pass        fused tile pass: a thread block holds 2^TB amplitudes whose
-//                 other spins are fixed by the block index (Secs. 3.3-3.4),
-//                 rotates the window spins in registers, 2^RB amplitudes per
-//                 thread, applies a diagonal slot between two layers, and
-//                 writes the tile back: one HBM round trip per pass
+//   (the fused tile pass k_tile is in ts4_tile.cuh; this file holds the step
+//   descriptors and per-pass tables it shares with the host)
 //   k_sum_*       FP64-accumulating reductions for the observables (Sec. 4.2)
 #pragma once
 
@@ -78,18 +75,7 @@ __global__ void k_slot_basic(typename CT<R>::T *__restrict__ psi, uint64_t dim, 
     }
 }
 
-// ------------------------------------------------------------------ fused tile pass
-
-// Bank swizzle of the shared-memory tile: the 16-byte (8-byte amplitudes) or
-// 8-slot (16-byte amplitudes) bank group of element e is XORed with its higher
-// nibbles, so that a warp reading 32 amplitudes that differ in any 4 (3)
-// consecutive local bits hits distinct banks.  XOR-linear: phys(a ^ b) =
-// phys(a) ^ phys(b).
-template <int ES> __host__ __device__ constexpr uint32_t phys(uint32_t e)
-{
-    return ES == 8 ? (e ^ (((e >> 4) ^ (e >> 8) ^ (e >> 12) ^ (e >> 16)) & 15u))
-                   : (e ^ (((e >> 3) ^ (e >> 6) ^ (e >> 9) ^ (e >> 12) ^ (e >> 15)) & 7u));
-}
+// ------------------------------------------------------------------ fused tile pass: descriptors
 
 struct StepDesc {
     uint8_t k;          // chunk: register window starts at min(k * RB, TB - RB)
@@ -101,23 +87,26 @@ struct StepDesc {
 
 constexpr int kMaxSteps = 16;
 
-struct PassArgs {
-    int c, w, h;  // tile geometry (global bits [0,c) and [w,w+h))
-    int nsteps;
-    StepDesc steps[kMaxSteps];
-    Slot slot;
-    int has_slot;
-    int tab;      // index of the slot's local tables
-    HamDev ham;
-};
+// Most spins outside a tile: N <= 34 and tiles of at least 11 spins.
+constexpr int kMaxFrame = 24;
 
-// Per-(slot, geometry) tables, built on the host in FP64 (angles in units of pi):
-//   A[l*TB+m] = t * J^a_{pos l, pos m} / (4 pi) for the tile's local bits (symmetric)
-//   QK[j]     = exp(-i sum_{l<m in chunk} A s_l s_m) * i^{pcq popcount(j)} for
-//               the register chunk of the step that applies the slot
+// Per-(slot, tile geometry, register chunk) tables, built on the host in FP64 and
+// rounded to R.  Angle unit: radians for complex64, half-turns for complex128.
+//   A[l*TB+m]   = t J^a_{pos l, pos m} / 4 for the tile's local bits (symmetric)
+//   QK[j]       c64:  (hi, lo) of q(j) = sum_{l<m in chunk} A_lm s_l s_m
+//               c128: exp(-i q(j)) i^{pcq popcount(j)}
+//   G0[l]       = t h^a_{pos l} / 2
+//   GF[l*kMaxFrame+m] = t J^a_{pos l, fpos m} / 4, for the nf spins outside the
+//               tile (global positions fpos[m], increasing)
+// so that the field on tile spin l from the fixed spins of frame f is
+//   g_l(f) = G0[l] + sum_m GF[l][m] sigma_{fpos m}(f).
 template <typename R, int TB, int RB> struct PassTab {
     R A[TB * TB];
     typename CT<R>::T QK[1 << RB];
+    R G0[TB];
+    R GF[TB * kMaxFrame];
+    int fpos[kMaxFrame];
+    int nf;
 };
 
 template <int RB, typename C> __device__ __forceinline__ void wht_regs(C (&x)[1 << RB], int lo, int hi)
@@ -130,241 +119,6 @@ template <int RB, typename C> __device__ __forceinline__ void wht_regs(C (&x)[1 
                 if (!(j & (1 << b)))
                     bfly(x[j], x[j | (1 << b)]);
         }
-    }
-}
-
-template <typename R, int TB, int RB> struct PassShared {
-    R A[TB * TB];
-    R g[TB];
-    typename CT<R>::T QK[1 << RB];
-    R thFF;
-    int pcF;
-};
-
-// Factors of the slot for one thread's 2^RB amplitudes (local index base | j << W):
-//   F(j) = 2^{-e} i^{pcq pc(s)} exp(-i theta(s)),
-//   theta = theta_FF + sum_{l in tile} s_l g_l + sum_{l<m in tile} A_lm s_l s_m.
-// Everything that depends on the thread's own bits (base) is summed once per
-// thread: theta = ang + sum_{b<RB} s_b cb_b + q(j); then
-//   F(j) = flo[j mod 2^LO] * fhi[j >> LO] * QK[j]
-// with flo, fhi products of exp(-+i cb_b) over the low / high register bits and
-// QK[j] = exp(-i q(j)) i^{pcq popcount(j)} from the per-slot table.
-template <typename R, int RB> struct SlotFactors {
-    static constexpr int LO = RB - 2;
-    typename CT<R>::T flo[1 << LO];
-    typename CT<R>::T fhi[4];
-};
-
-template <typename R, int TB, int RB, int W>
-__device__ __forceinline__ void slot_factors(SlotFactors<R, RB> &F, uint32_t base,
-                                             const PassShared<R, TB, RB> &sh, int pcq, R scale)
-{
-    using C = typename CT<R>::T;
-    constexpr int LO = RB - 2;
-    R ang = sh.thFF;
-    R cb[RB];
-#pragma unroll
-    for (int b = 0; b < RB; b++)
-        cb[b] = sh.g[W + b];
-#pragma unroll
-    for (int m = 0; m < TB; m++) {
-        if (m >= W && m < W + RB)
-            continue;
-        const R sm = ((base >> m) & 1u) ? R(1) : R(-1);
-        ang += sm * sh.g[m];
-#pragma unroll
-        for (int l = m + 1; l < TB; l++) {
-            if (l >= W && l < W + RB)
-                continue;
-            const R sl = ((base >> l) & 1u) ? R(1) : R(-1);
-            ang += (sm * sl) * sh.A[m * TB + l];
-        }
-#pragma unroll
-        for (int b = 0; b < RB; b++)
-            cb[b] += sm * sh.A[(W + b) * TB + m];
-    }
-    C eb = cexpm_pi(ang);
-    eb.x *= scale;
-    eb.y *= scale;
-    eb = cmul_ipow(eb, pcq * (sh.pcF + __popc(base)));
-    F.flo[0] = eb;
-#pragma unroll
-    for (int b = 0; b < LO; b++) {
-        const C ub = cexpm_pi(cb[b]);
-#pragma unroll
-        for (int k = 0; k < (1 << b); k++) {
-            const C v = F.flo[k];
-            F.flo[k] = cmul(v, cconj(ub));
-            F.flo[k | (1 << b)] = cmul(v, ub);
-        }
-    }
-    const C a1 = cexpm_pi(cb[LO]), b1 = cexpm_pi(cb[LO + 1]);
-    const C a0 = cconj(a1), b0 = cconj(b1);
-    F.fhi[0] = cmul(a0, b0);
-    F.fhi[1] = cmul(a1, b0);
-    F.fhi[2] = cmul(a0, b1);
-    F.fhi[3] = cmul(a1, b1);
-}
-
-template <typename R, int TB, int RB, int K, bool PH>
-__device__ __forceinline__ void run_step(typename CT<R>::T *tile, const StepDesc &d,
-                                         const PassShared<R, TB, RB> &sh, int pcq, R scale)
-{
-    using C = typename CT<R>::T;
-    constexpr int ES = sizeof(C);
-    constexpr int W = (K * RB < TB - RB) ? K * RB : TB - RB;
-    constexpr int LO = RB - 2;
-    const uint32_t tid = threadIdx.x;
-    const uint32_t base = (tid & ((1u << W) - 1)) | ((tid >> W) << (W + RB));
-    const uint32_t pb = phys<ES>(base);
-    SlotFactors<R, RB> F;
-    if constexpr (PH)
-        slot_factors<R, TB, RB, W>(F, base, sh, pcq, scale);
-    C x[1 << RB];
-#pragma unroll
-    for (int j = 0; j < (1 << RB); j++)
-        x[j] = tile[pb ^ phys<ES>((uint32_t)j << W)];
-    wht_regs<RB>(x, d.r0lo, d.r0hi);
-    if constexpr (PH) {
-#pragma unroll
-        for (int j = 0; j < (1 << RB); j++)
-            x[j] = cmul(x[j], cmul(cmul(F.flo[j & ((1 << LO) - 1)], F.fhi[j >> LO]), sh.QK[j]));
-    }
-    wht_regs<RB>(x, d.r1lo, d.r1hi);
-#pragma unroll
-    for (int j = 0; j < (1 << RB); j++)
-        tile[pb ^ phys<ES>((uint32_t)j << W)] = x[j];
-}
-
-// 128 registers per thread at most: as many blocks per SM as that allows
-template <int NT> constexpr int min_blocks() { return (512 / NT) > 0 ? (512 / NT) : 1; }
-
-template <typename R, int TB, int RB>
-__global__ void __launch_bounds__(1 << (TB - RB), min_blocks<(1 << (TB - RB))>())
-k_pass(typename CT<R>::T *__restrict__ psi, const __grid_constant__ PassArgs a,
-       const PassTab<R, TB, RB> *__restrict__ tabs)
-{
-    using C = typename CT<R>::T;
-    constexpr int ES = sizeof(C);
-    constexpr int NT = 1 << (TB - RB);
-    constexpr int NE = 1 << TB;
-    constexpr int NR = 1 << RB;
-    constexpr int PER_VEC = 16 / ES;         // amplitudes per 16-byte vector
-    constexpr int NV = NE / PER_VEC / NT;    // vectors per thread
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *tile = reinterpret_cast<C *>(smem_raw);
-    __shared__ PassShared<R, TB, RB> sh;
-
-    const int tid = threadIdx.x;
-    const uint64_t f = blockIdx.x;
-    const int c = a.c, w = a.w, h = a.h;
-    const uint64_t gbase = tile_global_index(c, w, h, f, 0);
-    const uint32_t cm = (1u << c) - 1u;
-    // local index step between the two amplitudes of one 16-byte vector
-    const uint32_t estep = (c >= 1) ? (1u << h) : 1u;
-
-    // ---- load: 16-byte vectors, consecutive threads on consecutive addresses (two batches)
-#pragma unroll
-    for (int half = 0; half < 2; half++) {
-        constexpr int NH = NV / 2;
-        float4 v[NH];
-#pragma unroll
-        for (int q = 0; q < NH; q++) {
-            const uint32_t u = (uint32_t)((half * NH + q) * NT + tid) * PER_VEC;
-            const uint64_t gi = gbase | (u & cm) | ((uint64_t)(u >> c) << w);
-            v[q] = __ldcs(reinterpret_cast<const float4 *>(psi + gi));
-        }
-#pragma unroll
-        for (int q = 0; q < NH; q++) {
-            const uint32_t u = (uint32_t)((half * NH + q) * NT + tid) * PER_VEC;
-            const uint32_t e = (u >> c) | ((u & cm) << h);
-            if constexpr (PER_VEC == 2) {
-                const float2 *p = reinterpret_cast<const float2 *>(&v[q]);
-                reinterpret_cast<float2 *>(tile)[phys<ES>(e)] = p[0];
-                reinterpret_cast<float2 *>(tile)[phys<ES>(e + estep)] = p[1];
-            } else {
-                reinterpret_cast<float4 *>(tile)[phys<ES>(e)] = v[q];
-            }
-        }
-    }
-
-    // ---- per-block part of the slot, FP64 (fixed spins of this block)
-    int pcq = 0;
-    R scale = R(1);
-    if (a.has_slot) {
-        const int N = a.ham.N;
-        const int al = a.slot.alpha;
-        const double t = a.slot.t;
-        const double *Jq = a.ham.Jq + (size_t)al * N * N;
-        const double *hh = a.ham.hh + (size_t)al * N;
-        pcq = a.slot.pcq;
-        scale = (R)ldexp(a.slot.mag, -a.slot.scale_exp);
-        if (tid < TB) {
-            const int pos = (tid < h) ? (w + tid) : (tid - h);
-            double acc = hh[pos];
-            for (int j = 0; j < N; j++)
-                if (!in_tile(j, c, w, h))
-                    acc += Jq[pos * N + j] * (((gbase >> j) & 1) ? 1.0 : -1.0);
-            sh.g[tid] = (R)(t * acc * 0.31830988618379067153776752674503);
-        } else if (tid >= 32 && tid < 64) {
-            const int lane = tid - 32;
-            double acc = 0.0;
-            for (int i = lane; i < N; i += 32) {
-                if (in_tile(i, c, w, h))
-                    continue;
-                double r = hh[i];
-                for (int j = i + 1; j < N; j++)
-                    if (!in_tile(j, c, w, h))
-                        r += Jq[i * N + j] * (((gbase >> j) & 1) ? 1.0 : -1.0);
-                acc += (((gbase >> i) & 1) ? 1.0 : -1.0) * r;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) {
-                sh.thFF = (R)halfturns_2pi(t * acc + a.slot.th0);
-                sh.pcF = __popcll(gbase);
-            }
-        }
-        const PassTab<R, TB, RB> *tb = tabs + a.tab;
-        for (int k = tid; k < TB * TB; k += NT)
-            sh.A[k] = tb->A[k];
-        if (tid < NR)
-            sh.QK[tid] = tb->QK[tid];
-    }
-    __syncthreads();
-
-    // ---- register-chunk steps
-    for (int s = 0; s < a.nsteps; s++) {
-        const StepDesc d = a.steps[s];
-        switch (d.k * 2 + (d.ph ? 1 : 0)) {
-        case 0: run_step<R, TB, RB, 0, false>(tile, d, sh, pcq, scale); break;
-        case 1: run_step<R, TB, RB, 0, true>(tile, d, sh, pcq, scale); break;
-        case 2: run_step<R, TB, RB, 1, false>(tile, d, sh, pcq, scale); break;
-        case 3: run_step<R, TB, RB, 1, true>(tile, d, sh, pcq, scale); break;
-        case 4: run_step<R, TB, RB, 2, false>(tile, d, sh, pcq, scale); break;
-        case 5: run_step<R, TB, RB, 2, true>(tile, d, sh, pcq, scale); break;
-        case 6: run_step<R, TB, RB, 3, false>(tile, d, sh, pcq, scale); break;
-        default: run_step<R, TB, RB, 3, true>(tile, d, sh, pcq, scale); break;
-        }
-        __syncthreads();
-    }
-
-    // ---- store
-#pragma unroll
-    for (int k = 0; k < NV; k++) {
-        const uint32_t u = (uint32_t)(k * NT + tid) * PER_VEC;
-        const uint32_t e = (u >> c) | ((u & cm) << h);
-        const uint64_t gi = gbase | (u & cm) | ((uint64_t)(u >> c) << w);
-        float4 v;
-        if constexpr (PER_VEC == 2) {
-            float2 *p = reinterpret_cast<float2 *>(&v);
-            p[0] = reinterpret_cast<const float2 *>(tile)[phys<ES>(e)];
-            p[1] = reinterpret_cast<const float2 *>(tile)[phys<ES>(e + estep)];
-        } else {
-            v = reinterpret_cast<const float4 *>(tile)[phys<ES>(e)];
-        }
-        __stcs(reinterpret_cast<float4 *>(psi + gi), v);
     }
 }
 

@@ -87,7 +87,32 @@ struct TileArgs {
     int exact_sincos;   // c64 per-amplitude factor: 0 if |y| <= 0.05, 1 if |y| <= 0.5, 2 otherwise (sincospif)
     IOLayout io;
     HamDev ham;
+    const double *theta; // per frame f: t E_FF(f) + th0 in half-turns, reduced to [-1, 1] (k_frame_theta)
 };
+
+// The frame part of a slot's angle, one value per tile f of a geometry (c, w, h):
+// theta[f] = (t E_FF(f) + th0) / pi reduced mod 2, where E_FF collects the field and
+// coupling terms among the spins outside the tile.  FP64, computed once per
+// schedule; the passes read one value per block.
+__global__ void k_frame_theta(const double *__restrict__ Jq, const double *__restrict__ hh, int N, int c, int w,
+                              int h, double t, double th0, uint64_t nframes, double *__restrict__ theta)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nframes; f += stride) {
+        const uint64_t gb = tile_global_index(c, w, h, f, 0);
+        double acc = 0.0;
+        for (int i = 0; i < N; i++) {
+            if (in_tile(i, c, w, h))
+                continue;
+            double r = hh[i];
+            for (int j = i + 1; j < N; j++)
+                if (!in_tile(j, c, w, h))
+                    r += Jq[i * N + j] * (((gb >> j) & 1) ? 1.0 : -1.0);
+            acc += (((gb >> i) & 1) ? 1.0 : -1.0) * r;
+        }
+        theta[f] = halfturns_2pi(t * acc + th0);
+    }
+}
 
 // Per-(slot, group) tables (host, FP64):
 //   c64 : A = t J / 4 on local bits (radians); Q[j] = (hi, lo) of the in-chunk quadratic term (radians)
@@ -457,54 +482,35 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
         x[j] = __ldcs(psi + gi);
     }
 
-    // ---- per-block part of the slot, FP64
+    // ---- per-block part of the slot: frame angle (precomputed, FP64) and fields g_l
     int pcq = 0;
     R scale = R(1);
     float srel = 0.0f;                 // exact scale / rounded scale - 1 (c64: sqrt 1/2 is not exact)
     const int mode = a.exact_sincos;   // c64 per-amplitude factor: 0 tiny |y|, 1 small |y|, 2 any
     if (a.has_slot) {
-        const int N = a.ham.N;
-        const int al = a.slot.alpha;
-        const double t = a.slot.t;
-        const double *Jq = a.ham.Jq + (size_t)al * N * N;
-        const double *hh = a.ham.hh + (size_t)al * N;
         pcq = a.slot.pcq;
         const double sx = ldexp(a.slot.mag, -a.slot.scale_exp);
         scale = (R)sx;
         srel = (float)(sx / (double)scale - 1.0);
-        // g in radians (c64) or half-turns (c128)
-        const double gunit = (sizeof(R) == 4) ? 1.0 : 0.31830988618379067153776752674503;
-        if (tid < TB) {
-            const int pos = gpos(tid);
-            double acc = hh[pos];
-            for (int j = 0; j < N; j++)
-                if (!in_tile(j, c, w, h))
-                    acc += Jq[pos * N + j] * (((gbase >> j) & 1) ? 1.0 : -1.0);
-            sh.g[tid] = (R)(t * acc * gunit);
-        } else if (tid >= 32 && tid < 64) {
-            const int lane = tid - 32;
-            double acc = 0.0;
-            for (int i = lane; i < N; i += 32) {
-                if (in_tile(i, c, w, h))
-                    continue;
-                double r = hh[i];
-                for (int j = i + 1; j < N; j++)
-                    if (!in_tile(j, c, w, h))
-                        r += Jq[i * N + j] * (((gbase >> j) & 1) ? 1.0 : -1.0);
-                acc += (((gbase >> i) & 1) ? 1.0 : -1.0) * r;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) {
-                const double th = halfturns_2pi(t * acc + a.slot.th0);
-                sh.th = th;
-                sh.th_hi = (float)th;
-                sh.th_lo = (float)(th - (double)(float)th);
-                sh.pcF = __popcll(gbase);
-            }
-        }
         const TileTab<R, TB, RB> *tb = tabs + a.tab;
+        // field on each tile spin from the frame spins (table terms, R precision)
+        if (tid < TB) {
+            R acc = tb->G0[tid];
+            const int nf = tb->nf;
+#pragma unroll
+            for (int m = 0; m < kMaxFrame; m++)
+                if (m < nf) {
+                    const R v = tb->GF[tid * kMaxFrame + m];
+                    acc += ((gbase >> tb->fpos[m]) & 1) ? v : -v;
+                }
+            sh.g[tid] = acc;
+        } else if (tid == 32) {
+            const double th = a.theta[f];
+            sh.th = th;
+            sh.th_hi = (float)th;
+            sh.th_lo = (float)(th - (double)(float)th);
+            sh.pcF = __popcll(gbase);
+        }
         for (int k = tid; k < TB * TB; k += K::NT)
             sh.A[k] = tb->A[k];
         if (tid < NR)
