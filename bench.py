@@ -31,6 +31,39 @@ WORKLOAD = "N=28 open chain, dipolar XXZ (J^z=1/|i-j|^3, J^x=J^y=-J^z/2, 378 bon
 TAU = 0.01
 
 
+KERNEL_SOURCES = ("paper_1305_0036_gb300/csrc/ts4_tile.cuh", "paper_1305_0036_gb300/csrc/ts4_kernels.cuh",
+                  "paper_1305_0036_gb300/csrc/ts4_common.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_tile_traffic.txt")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(N):
+    """DRAM bytes per k_tile launch from the committed ncu summary, scaled to 2^N amplitudes;
+    None when the kernel sources changed since the counters were taken."""
+    try:
+        kv = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                line = line.strip()
+                if line and not line.startswith("#"):
+                    k, v = line.split(None, 1)
+                    kv[k] = v.strip()
+        if kv.get("source_sha256") != kernel_source_hash():
+            return None
+        n0 = int(kv["spins"])
+        return float(kv["dram_bytes_per_launch"]) * 2.0 ** (N - n0)
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -194,7 +227,7 @@ def run_ours(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    s = W.dipolar_chain(28)
+    s = W.dipolar_chain(args.spins)
     N = s.N
     prec = args.prec
     npdt = np.complex64 if prec == "c64" else np.complex128
@@ -266,14 +299,15 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": "TS4 steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": prec, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N, "prec": prec, "tile_bits": sched["tile_bits"],
+        "config": {"workload": WORKLOAD if N == 28 else WORKLOAD.replace("N=28", f"N={N}"), "N": N, "prec": prec, "tile_bits": sched["tile_bits"],
                    "coalesce_bits": sched["coalesce_bits"], "groups": groups, "passes_per_step": passes,
-                   "l2": "state 2^28 amplitudes >> 129 MB L2 (no flush needed)",
+                   "l2": f"state {state_bytes / 2**20:.0f} MiB vs 129 MB L2" +
+                         (" (larger: no flush needed)" if state_bytes > 2 * 129e6 else " (NOT larger than L2)"),
                    "parallelism": f"replicas x{ws}"},
         "hbm": {"effective_gbs": eff_gbs, "effective_frac": eff_gbs / peak,
                 "pass_traffic_gbs": dram_gbs, "pass_traffic_frac": dram_gbs / peak},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / peak, "traffic": measured_traffic(N), "peak_kind": peak_kind,
                      "kernel": "k_tile", "alg_bytes_per_launch": alg_bytes_launch,
                      "avg_launch_ms": avg_pass_ms},
         "e2e": {"value": e2e_value, "unit": "TS4 steps/s", "h2d_bytes_per_step": state_bytes / args.steps,
@@ -319,6 +353,8 @@ def main():
     ap.add_argument("--compare-c128", action="store_true", default=True)
     ap.add_argument("--no-compare-c128", dest="compare_c128", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--spins", type=int, default=28,
+                    help="chain length N (28 is the benchmark; smaller N only for profiling captures)")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":

@@ -46,6 +46,9 @@ struct HostSlot {
         s.pcq = pcq;
         s.scale_exp = scale_exp;
         s.pad = 0;
+        s.scale = std::ldexp(mag, -scale_exp);
+        s.scale_f = (float)s.scale;
+        s.srel = (float)(s.scale / (double)s.scale_f - 1.0);
         return s;
     }
 };
@@ -168,7 +171,7 @@ bool tile_supported(ts_prec p, int tb)
 {
     return p == TS_C64 ? (tb >= 12 && tb <= 14) : (tb >= 11 && tb <= 13);
 }
-int default_tile(ts_prec p) { return p == TS_C64 ? 13 : 12; }
+int default_tile(ts_prec) { return 12; }  // fastest at N=28 on GB300 for both precisions (measured)
 int default_cbits(ts_prec p) { return p == TS_C64 ? 3 : 2; }
 
 template <typename R, int TB, int RB>
@@ -219,8 +222,8 @@ size_t tab_size(ts_prec p, int TB)
 }
 
 // Host FP64 construction of the per-(slot, group) tables of the tile kernel.
-//   c64 : A = t J/4 on the tile's local bits (radians); Q[j] = (hi, lo) float pair of
-//         q(j) = sum_{l<m in chunk} A_lm s_l s_m (radians); the i^{pcq popcount(j)} part is
+//   c64 : A = t J/4 on the tile's local bits (radians); Q[j].x = q(j) =
+//         sum_{l<m in chunk} A_lm s_l s_m (radians); the i^{pcq popcount(j)} part is
 //         applied in the kernel.
 //   c128: A in half-turns; Q[j] = exp(-i q(j)) i^{pcq popcount(j)}.
 template <typename R, int TB, int RB>
@@ -268,7 +271,7 @@ void build_tab_t(unsigned char *dst, const ts_ctx *ctx, const HostSlot &sl, cons
         C z;
         if (f32) {
             z.x = (R)q;
-            z.y = (R)(q - (double)(float)q);
+            z.y = (R)0;
         } else {
             double re = std::cos(q), im = -std::sin(q);
             const int k = (sl.pcq * __builtin_popcount((unsigned)j)) & 3;
@@ -510,12 +513,29 @@ ChunkInfo chunks_of(int h, int TB, int RB)
 
 enum PassKind { P_PHASE_ROT, P_ROT, P_ROT_PHASE_ROT, P_ROT_PHASE, P_PHASE };
 
+// Chunk whose register bits the I/O layout of group g uses: the lanes must sit on the
+// globally lowest bits of the tile, which for the lowest group (c == 0) are the first
+// RB local bits, so there the registers take chunk 1; otherwise the lowest bits are the
+// c coalescing bits (local bits h..TB-1) and the registers take chunk 0.
+int io_chunk(const Group &g) { return g.c == 0 ? 1 : 0; }
+
+// One pass over group g.  The layer's chunks are visited starting from the I/O chunk
+// (the tile arrives and leaves in that layout), so a pass that rotates the group twice
+// around a slot costs 4 transposes for three chunks instead of 6:
+// io, a, b | slot | b, a, io.
 HostPass make_pass(int gi, const Group &g, PassKind kind, int slot, int TB, int RB)
 {
     HostPass p;
     p.group = gi;
     p.slot = slot;
     ChunkInfo ci = chunks_of(g.h, TB, RB);
+    const int n = ci.n;
+    const int kio = io_chunk(g) < n ? io_chunk(g) : 0;
+    int ord[8];
+    ord[0] = kio;
+    for (int k = 0, m = 1; k < n; k++)
+        if (k != kio)
+            ord[m++] = k;
     auto add = [&](int k, bool r0, bool ph, bool r1) {
         StepDesc d;
         std::memset(&d, 0, sizeof(d));
@@ -529,31 +549,30 @@ HostPass make_pass(int gi, const Group &g, PassKind kind, int slot, int TB, int 
             p.phase_k = k;
         p.steps[p.nsteps++] = d;
     };
-    const int n = ci.n;
     switch (kind) {
     case P_PHASE_ROT:
-        add(0, false, true, true);
-        for (int k = 1; k < n; k++)
-            add(k, true, false, false);
+        add(ord[0], false, true, true);
+        for (int i = 1; i < n; i++)
+            add(ord[i], true, false, false);
         break;
     case P_ROT:
-        for (int k = 0; k < n; k++)
-            add(k, true, false, false);
+        for (int i = 0; i < n; i++)
+            add(ord[i], true, false, false);
         break;
     case P_ROT_PHASE_ROT:
-        for (int k = 0; k < n - 1; k++)
-            add(k, true, false, false);
-        add(n - 1, true, true, true);
-        for (int k = n - 2; k >= 0; k--)
-            add(k, true, false, false);
+        for (int i = 0; i < n - 1; i++)
+            add(ord[i], true, false, false);
+        add(ord[n - 1], true, true, true);
+        for (int i = n - 2; i >= 0; i--)
+            add(ord[i], false, false, true);
         break;
     case P_ROT_PHASE:
-        for (int k = 0; k < n - 1; k++)
-            add(k, true, false, false);
-        add(n - 1, true, true, false);
+        for (int i = 1; i < n; i++)
+            add(ord[i], true, false, false);
+        add(ord[0], true, true, false);
         break;
     case P_PHASE:
-        add(0, false, true, false);
+        add(ord[0], false, true, false);
         break;
     }
     return p;
@@ -684,7 +703,7 @@ ts_status prepare_fused(ts_ctx *ctx, Schedule &S)
     S.groups = make_groups(ctx->N, TB, ctx->cbits);
     S.io.clear();
     for (size_t gi = 0; gi < S.groups.size(); gi++)
-        S.io.push_back(make_io(S.groups[gi], TB, RB, ES, S.groups[gi].c == 0 ? 1 : 0));
+        S.io.push_back(make_io(S.groups[gi], TB, RB, ES, io_chunk(S.groups[gi])));
     const int64_t L = (int64_t)S.slots.size() - 1;
     S.passes = make_passes(S.groups, L, TB, RB);
     S.tab_size = tab_size(ctx->prec, TB);

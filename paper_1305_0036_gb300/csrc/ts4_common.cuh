@@ -55,17 +55,15 @@ template <typename C> __host__ __device__ __forceinline__ C cmul_ipow(C a, int k
     return r;
 }
 
-// Unnormalised butterfly W on a pair (x0 = bit 0, x1 = bit 1): (x0 + x1, x0 - x1).
+// Unnormalised butterfly W on a pair (x0 = bit 0, x1 = bit 1): (x0 + x1, x0 - x1),
+// with the packed FP32x2 instructions (one per complex add; a - b as a + b * (-1),
+// which rounds once like the plain subtraction).
 __device__ __forceinline__ void bfly(float2 &a, float2 &b)
 {
-    // packed FP32x2 arithmetic (one instruction per complex add)
-    unsigned long long ua, ub, us, ud;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(ua) : "f"(a.x), "f"(a.y));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(ub) : "f"(b.x), "f"(b.y));
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(us) : "l"(ua), "l"(ub));
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(ud) : "l"(ua), "l"(ub));
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(us));
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(b.x), "=f"(b.y) : "l"(ud));
+    const float2 s = __fadd2_rn(a, b);
+    const float2 d = __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+    a = s;
+    b = d;
 }
 __device__ __forceinline__ void bfly(double2 &a, double2 &b)
 {
@@ -107,6 +105,9 @@ struct Slot {
     int pcq;        // 0..3
     int scale_exp;  // exact power-of-two scale
     int pad;
+    double scale;   // mag 2^{-scale_exp} (host-computed: no FP64 arithmetic in the kernels)
+    float scale_f;  // the same, rounded to FP32
+    float srel;     // scale / scale_f - 1, the rounding of scale_f (0 unless mag = sqrt 1/2)
 };
 
 // Device copies of the Hamiltonian, FP64:

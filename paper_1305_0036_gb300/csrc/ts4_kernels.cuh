@@ -53,7 +53,7 @@ __global__ void k_slot_basic(typename CT<R>::T *__restrict__ psi, uint64_t dim, 
     using C = typename CT<R>::T;
     const double *Jq = ham.Jq + (size_t)sl.alpha * ham.N * ham.N;
     const double *hh = ham.hh + (size_t)sl.alpha * ham.N;
-    const double scale = ldexp(sl.mag, -sl.scale_exp);
+    const double scale = sl.scale;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < dim; s += stride) {
         double th = sl.th0;
@@ -93,7 +93,7 @@ constexpr int kMaxFrame = 24;
 // Per-(slot, tile geometry, register chunk) tables, built on the host in FP64 and
 // rounded to R.  Angle unit: radians for complex64, half-turns for complex128.
 //   A[l*TB+m]   = t J^a_{pos l, pos m} / 4 for the tile's local bits (symmetric)
-//   QK[j]       c64:  (hi, lo) of q(j) = sum_{l<m in chunk} A_lm s_l s_m
+//   QK[j]       c64:  (q(j), 0) with q(j) = sum_{l<m in chunk} A_lm s_l s_m
 //               c128: exp(-i q(j)) i^{pcq popcount(j)}
 //   G0[l]       = t h^a_{pos l} / 2
 //   GF[l*kMaxFrame+m] = t J^a_{pos l, fpos m} / 4, for the nf spins outside the

@@ -114,9 +114,7 @@ __global__ void k_frame_theta(const double *__restrict__ Jq, const double *__res
     }
 }
 
-// Per-(slot, group) tables (host, FP64):
-//   c64 : A = t J / 4 on local bits (radians); Q[j] = (hi, lo) of the in-chunk quadratic term (radians)
-//   c128: A in half-turns; Q[j] = exp(-i q(j)) i^{pcq popcount(j)} (as in PassTab)
+// Per-(slot, group) tables: PassTab (host-built in FP64, see ts4_kernels.cuh)
 template <typename R, int TB, int RB> using TileTab = PassTab<R, TB, RB>;
 
 struct SlotThreadC64 {
@@ -131,9 +129,48 @@ struct SlotThreadC128 {
     double2 fhi[4];
 };
 
+// The per-thread factors live in shared memory between their computation and the
+// slot step, one array per field ([field][thread]), so that a warp reading one
+// field touches consecutive words: an array of the structs above (stride 104 or
+// 128 bytes) would put several lanes of a warp on the same bank.
+template <int NT> struct SlotSoA64 {
+    float2 R[6][NT];
+    float Lo[8][NT];
+    float Hi[4][NT];
+    float kT[NT];
+
+    __device__ __forceinline__ void put(int t, const SlotThreadC64 &o)
+    {
+#pragma unroll
+        for (int k = 0; k < 6; k++)
+            R[k][t] = o.R[k];
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            Lo[k][t] = o.Lo[k];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            Hi[k][t] = o.Hi[k];
+        kT[t] = o.kT;
+    }
+};
+
+template <int NT> struct SlotSoA128 {
+    double2 flo[4][NT];
+    double2 fhi[4][NT];
+
+    __device__ __forceinline__ void put(int t, const SlotThreadC128 &o)
+    {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            flo[k][t] = o.flo[k];
+            fhi[k][t] = o.fhi[k];
+        }
+    }
+};
+
 template <typename R, int TB, int RB> struct TileShared {
     // per-thread slot factors, computed before the tile occupies the registers
-    typename std::conditional<sizeof(R) == 4, SlotThreadC64, SlotThreadC128>::type th_f[1 << (TB - RB)];
+    typename std::conditional<sizeof(R) == 4, SlotSoA64<1 << (TB - RB)>, SlotSoA128<1 << (TB - RB)>>::type th_f;
     R A[TB * TB];
     R g[TB];
     typename CT<R>::T Q[1 << RB];
@@ -254,26 +291,21 @@ __device__ __forceinline__ void slot_thread_c64(SlotThreadC64 &o, uint32_t base,
     }
 }
 
-// e^{-iy} = (1 + c) - i s with s = sin y and c = cos y - 1, |(1 + c, s)| = 1 to ~1e-14:
-// mode 0 (|y| <= 0.05): s from its Taylor series, c = -(1 - sqrt(1 - s^2)) from the
-//   binomial series in u = s^2 (truncation < 2e-12), so that the pair stays on the unit circle;
-// mode 1 (|y| <= 0.5): Taylor series of both, then the magnitude error d = 2c + c^2 + s^2
+// e^{-iy} = (1 + c) - i s with s = sin y and c = cos y - 1, kept on the unit circle:
+// mode 0 (|y| <= 0.05): Taylor series of cos y - 1 to y^6 and of sin y to y^5; the
+//   magnitude error of the exact pair, 2 c_err + 2 s s_err, is below 2e-14, and the FP32
+//   rounding of c (|c| <= 1.25e-3) adds about 1e-10;
+// mode 1 (|y| <= 0.5): series to y^10 / y^11, then the magnitude error d = 2c + c^2 + s^2
 //   is removed to first order;
 // mode 2 (any y): CUDA's sincospif, then the same correction.
 template <int MODE> __device__ __forceinline__ void unit_factor(float y, float &c, float &s)
 {
+    const float y2 = y * y;
     if constexpr (MODE == 0) {
-        const float y2 = y * y;
-        float ps = fmaf(y2, 1.0f / 120.0f, -1.0f / 6.0f);
-        ps = fmaf(y2, ps, 1.0f);
-        s = y * ps;
-        const float u = s * s;
-        float pc = fmaf(u, 1.0f / 16.0f, 1.0f / 8.0f);
-        pc = fmaf(u, pc, 0.5f);
-        c = -u * pc;
+        c = y2 * fmaf(y2, fmaf(y2, -1.0f / 720.0f, 1.0f / 24.0f), -0.5f);
+        s = fmaf(y * y2, fmaf(y2, 1.0f / 120.0f, -1.0f / 6.0f), y);
     } else {
         if constexpr (MODE == 1) {
-            const float y2 = y * y;
             float pc = fmaf(y2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
             pc = fmaf(y2, pc, -1.0f / 720.0f);
             pc = fmaf(y2, pc, 1.0f / 24.0f);
@@ -283,8 +315,7 @@ template <int MODE> __device__ __forceinline__ void unit_factor(float y, float &
             ps = fmaf(y2, ps, -1.0f / 5040.0f);
             ps = fmaf(y2, ps, 1.0f / 120.0f);
             ps = fmaf(y2, ps, -1.0f / 6.0f);
-            ps = fmaf(y2, ps, 1.0f);
-            s = y * ps;
+            s = fmaf(y * y2, ps, y);
         } else {
             float cc;
             sincospif(y * 0.31830988618379067f, &s, &cc);
@@ -296,38 +327,36 @@ template <int MODE> __device__ __forceinline__ void unit_factor(float y, float &
     }
 }
 
-// Per-amplitude factors: x_j <- (x_j R[popcount j]) ((1 + c_j) - i s_j).  Every factor has
-// unit magnitude to ~1e-14 times the exact scale; the two FP32 roundings left are those of
-// products with x_j, which change from step to step, so they do not build up coherently.
-template <int RB, int MODE>
-__device__ __forceinline__ void slot_c64_apply(float2 (&x)[1 << RB], const SlotThreadC64 &o,
+// Per-amplitude factors: x_j <- (x_j R[popcount j]) ((1 + c_j + kT) - i s_j).  Every factor
+// has unit magnitude to ~1e-10 times the exact scale (the dropped terms kT c and kT s of the
+// exact product (1 + kT)((1 + c) - i s) change it by < 2e-10); the FP32 roundings left are
+// those of products with x_j, which change from step to step and do not build up.
+template <int RB, int MODE, int NT>
+__device__ __forceinline__ void slot_c64_apply(float2 (&x)[1 << RB], const SlotSoA64<NT> &o, int t,
                                                const float2 *__restrict__ Q)
 {
-    const float kT = o.kT;
+    const float kT = o.kT[t];
 #pragma unroll
     for (int j = 0; j < (1 << RB); j++) {
-        const float2 qv = Q[j];
-        const float y = ((o.Lo[j & 7] + o.Hi[j >> 3]) + qv.x) + qv.y;
+        const float y = (o.Lo[j & 7][t] + o.Hi[j >> 3][t]) + Q[j].x;
         float c, s;
         unit_factor<MODE>(y, c, s);
-        // fold T's magnitude correction: (1 + c)(1 + kT) = 1 + (c + kT + c kT)
-        const float ct = fmaf(c, kT, c + kT);
-        const float st = fmaf(s, kT, s);
-        const float2 x1 = cmul(x[j], o.R[popc_c(j)]);
-        x[j] = make_float2(fmaf(x1.x, ct, fmaf(x1.y, st, x1.x)), fmaf(x1.y, ct, fmaf(-x1.x, st, x1.y)));
+        const float ct = c + kT;
+        const float2 x1 = cmul(x[j], o.R[popc_c(j)][t]);
+        x[j] = make_float2(fmaf(x1.x, ct, fmaf(x1.y, s, x1.x)), fmaf(x1.y, ct, fmaf(-x1.x, s, x1.y)));
     }
 }
 
-template <int RB>
-__device__ __forceinline__ void slot_c64(float2 (&x)[1 << RB], const SlotThreadC64 &o, const float2 *__restrict__ Q,
-                                         int mode)
+template <int RB, int NT>
+__device__ __forceinline__ void slot_c64(float2 (&x)[1 << RB], const SlotSoA64<NT> &o, int t,
+                                         const float2 *__restrict__ Q, int mode)
 {
     if (mode == 0)
-        slot_c64_apply<RB, 0>(x, o, Q);
+        slot_c64_apply<RB, 0>(x, o, t, Q);
     else if (mode == 1)
-        slot_c64_apply<RB, 1>(x, o, Q);
+        slot_c64_apply<RB, 1>(x, o, t, Q);
     else
-        slot_c64_apply<RB, 2>(x, o, Q);
+        slot_c64_apply<RB, 2>(x, o, t, Q);
 }
 
 // c128 slot: per-thread factors (errors ~1e-16; table of the in-chunk terms).
@@ -380,11 +409,13 @@ __device__ __forceinline__ void slot_thread_c128(SlotThreadC128 &o, uint32_t bas
     o.fhi[3] = cmul(a1, b1);
 }
 
-__device__ __forceinline__ void slot_c128(double2 (&x)[16], const SlotThreadC128 &o, const double2 *__restrict__ Q)
+template <int NT>
+__device__ __forceinline__ void slot_c128(double2 (&x)[16], const SlotSoA128<NT> &o, int t,
+                                          const double2 *__restrict__ Q)
 {
 #pragma unroll
     for (int j = 0; j < 16; j++)
-        x[j] = cmul(x[j], cmul(cmul(o.flo[j & 3], o.fhi[j >> 2]), Q[j]));
+        x[j] = cmul(x[j], cmul(cmul(o.flo[j & 3][t], o.fhi[j >> 2][t]), Q[j]));
 }
 
 template <typename R, int TB, int RB> struct TileKernel {
@@ -425,9 +456,9 @@ template <typename R, int TB, int RB> struct TileKernel {
     static __device__ __forceinline__ void apply_slot(C (&x)[NR], const TileShared<R, TB, RB> &sh, int mode)
     {
         if constexpr (sizeof(R) == 4)
-            slot_c64<RB>(x, sh.th_f[threadIdx.x], sh.Q, mode);
+            slot_c64<RB>(x, sh.th_f, threadIdx.x, sh.Q, mode);
         else
-            slot_c128(x, sh.th_f[threadIdx.x], sh.Q);
+            slot_c128(x, sh.th_f, threadIdx.x, sh.Q);
     }
 };
 
@@ -489,9 +520,12 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
     const int mode = a.exact_sincos;   // c64 per-amplitude factor: 0 tiny |y|, 1 small |y|, 2 any
     if (a.has_slot) {
         pcq = a.slot.pcq;
-        const double sx = ldexp(a.slot.mag, -a.slot.scale_exp);
-        scale = (R)sx;
-        srel = (float)(sx / (double)scale - 1.0);
+        if constexpr (sizeof(R) == 4) {
+            scale = a.slot.scale_f;
+            srel = a.slot.srel;
+        } else {
+            scale = a.slot.scale;
+        }
         const TileTab<R, TB, RB> *tb = tabs + a.tab;
         // field on each tile spin from the frame spins (table terms, R precision)
         if (tid < TB) {
@@ -524,10 +558,15 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
         for (int s = 0; s < a.nsteps; s++)
             if (a.steps[s].ph)
                 kph = a.steps[s].k;
-        if constexpr (sizeof(R) == 4)
-            slot_thread_c64<TB, RB>(sh.th_f[tid], base_of(kph), kph, sh, pcq, (float)scale, srel);
-        else
-            slot_thread_c128<TB, RB>(sh.th_f[tid], base_of(kph), chunk_w<TB, RB>(kph), sh, pcq, (double)scale);
+        if constexpr (sizeof(R) == 4) {
+            SlotThreadC64 o;
+            slot_thread_c64<TB, RB>(o, base_of(kph), kph, sh, pcq, (float)scale, srel);
+            sh.th_f.put(tid, o);
+        } else {
+            SlotThreadC128 o;
+            slot_thread_c128<TB, RB>(o, base_of(kph), chunk_w<TB, RB>(kph), sh, pcq, (double)scale);
+            sh.th_f.put(tid, o);
+        }
     }
 
     // ---- steps: transpose to the step's chunk layout when it changes
@@ -593,8 +632,15 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
     }
 }
 
+// Resident blocks per SM the register allocation is sized for: 64K registers hold
+// 2 blocks of 256 threads or 4 blocks of 128 threads at 128 registers each.
+__host__ __device__ constexpr int tile_min_blocks(int thread_bits)
+{
+    return thread_bits <= 7 ? 4 : (thread_bits <= 8 ? 2 : 1);
+}
+
 template <typename R, int TB, int RB>
-__global__ void __launch_bounds__(1 << (TB - RB), (TB - RB <= 8) ? 2 : 1)
+__global__ void __launch_bounds__(1 << (TB - RB), tile_min_blocks(TB - RB))
 k_tile(typename CT<R>::T *__restrict__ psi, const __grid_constant__ TileArgs a,
        const TileTab<R, TB, RB> *__restrict__ tabs)
 {
@@ -615,7 +661,7 @@ struct BatchSys {
 };
 
 template <typename R, int TB, int RB>
-__global__ void __launch_bounds__(1 << (TB - RB), (TB - RB <= 8) ? 2 : 1)
+__global__ void __launch_bounds__(1 << (TB - RB), tile_min_blocks(TB - RB))
 k_tile_batch(const BatchSys *__restrict__ sys, const TileArgs *__restrict__ args, int nsys)
 {
     const uint32_t b = blockIdx.x;
