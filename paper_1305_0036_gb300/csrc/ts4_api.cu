@@ -65,7 +65,7 @@ struct HostPass {
     int phase_k = 0;    // chunk of the step that applies the slot
     int tab = -1;
     int ymode = 0;      // c64 per-amplitude factor: 0 |y| <= 0.05, 1 |y| <= 0.5, 2 sincospif
-    size_t theta_off = 0; // first entry of this pass's frame-angle table in Schedule::dtheta
+    size_t theta_off = 0; // first frame of this pass's (slot, group) in Schedule::dtheta / dgfield
 };
 
 struct Schedule {
@@ -84,7 +84,8 @@ struct Schedule {
     void *dtab = nullptr;                // device copy, owned by this schedule
     size_t dtab_cap = 0;
     double *dtheta = nullptr;            // frame angles of every (slot, group), owned by this schedule
-    size_t dtheta_cap = 0;               // doubles
+    void *dgfield = nullptr;             // fields g_l per frame (TB values of the kernel's precision), same allocation
+    size_t dtheta_cap = 0;               // bytes of the allocation
 };
 
 // Frees S's device tables once the stream's queued passes (which read them) are done.
@@ -99,6 +100,7 @@ void release_tables(Schedule &S, cudaStream_t st)
     S.dtab = nullptr;
     S.dtab_cap = 0;
     S.dtheta = nullptr;
+    S.dgfield = nullptr;
     S.dtheta_cap = 0;
 }
 
@@ -221,17 +223,20 @@ size_t tab_size(ts_prec p, int TB)
     }
 }
 
-// Host FP64 construction of the per-(slot, group) tables of the tile kernel.
-//   c64 : A = t J/4 on the tile's local bits (radians); Q[j].x = q(j) =
-//         sum_{l<m in chunk} A_lm s_l s_m (radians); the i^{pcq popcount(j)} part is
-//         applied in the kernel.
-//   c128: A in half-turns; Q[j] = exp(-i q(j)) i^{pcq popcount(j)}.
+// Host FP64 construction of the per-(slot, group, chunk) tables of the tile kernel
+// (PassTab: the couplings among each thread's own bits, TP and TC, and the in-chunk
+// table QK).  The thread's bits are those of its base index in the layout of the
+// step that applies the slot: the I/O layout when that is the I/O chunk, the
+// chunk layout otherwise -- the same mapping from thread index to local bits as the
+// kernel's base_of().
 template <typename R, int TB, int RB>
-void build_tab_t(unsigned char *dst, const ts_ctx *ctx, const HostSlot &sl, const Group &g, int phase_k)
+void build_tab_t(unsigned char *dst, const ts_ctx *ctx, const HostSlot &sl, const Group &g, const IOLayout &io,
+                 int phase_k)
 {
     using C = typename CT<R>::T;
-    PassTab<R, TB, RB> tb;
-    std::memset(&tb, 0, sizeof(tb));
+    constexpr int NT = 1 << (TB - RB), ES = sizeof(C);
+    std::vector<unsigned char> buf(sizeof(PassTab<R, TB, RB>), 0);
+    PassTab<R, TB, RB> &tb = *reinterpret_cast<PassTab<R, TB, RB> *>(buf.data());
     const int N = ctx->N;
     const double *Jq = ctx->Jq.data() + (size_t)sl.alpha * N * N;
     auto pos = [&](int l) { return l < g.h ? g.w + l : l - g.h; };
@@ -242,24 +247,33 @@ void build_tab_t(unsigned char *dst, const ts_ctx *ctx, const HostSlot &sl, cons
                 A[l * TB + m] = sl.t * Jq[pos(l) * N + pos(m)];
     const bool f32 = sizeof(R) == 4;
     const double unit = f32 ? 1.0 : 1.0 / M_PI;
-    for (int k = 0; k < TB * TB; k++)
-        tb.A[k] = (R)(A[k] * unit);
-    // fields on the tile spins from the spins outside the tile
-    const double *hh = ctx->hh.data() + (size_t)sl.alpha * N;
-    std::vector<int> fpos;
-    for (int i = 0; i < N; i++)
-        if (!in_tile(i, g.c, g.w, g.h))
-            fpos.push_back(i);
-    tb.nf = (int)fpos.size();
-    for (int m = 0; m < tb.nf; m++)
-        tb.fpos[m] = fpos[m];
-    for (int l = 0; l < TB; l++) {
-        const int i = pos(l);
-        tb.G0[l] = (R)(sl.t * hh[i] * unit);
-        for (int m = 0; m < tb.nf; m++)
-            tb.GF[l * kMaxFrame + m] = (R)(sl.t * Jq[i * N + fpos[m]] * unit);
-    }
     const int W = chunk_w<TB, RB>(phase_k);
+    // thread bits of the slot's layout
+    int tbits[TB - RB];
+    if (phase_k == io.chunk) {
+        for (int t = 0; t < TB - RB; t++)
+            tbits[t] = io.bits[t];
+    } else {
+        const ChunkLayout<TB, RB, ES> L(W);
+        for (int t = 0; t < TB - RB; t++)
+            tbits[t] = L.bits[t];
+    }
+    for (int tid = 0; tid < NT; tid++) {
+        double sgn[TB - RB];
+        for (int t = 0; t < TB - RB; t++)
+            sgn[t] = ((tid >> t) & 1) ? 1.0 : -1.0;
+        double tp = 0.0;
+        for (int u = 0; u < TB - RB; u++)
+            for (int v = u + 1; v < TB - RB; v++)
+                tp += A[tbits[u] * TB + tbits[v]] * sgn[u] * sgn[v];
+        tb.TP[tid] = (R)(tp * unit);
+        for (int b = 0; b < RB; b++) {
+            double tc = 0.0;
+            for (int u = 0; u < TB - RB; u++)
+                tc += A[(W + b) * TB + tbits[u]] * sgn[u];
+            tb.TC[b][tid] = (R)(tc * unit);
+        }
+    }
     for (int j = 0; j < (1 << RB); j++) {
         double q = 0.0;
         for (int l = 0; l < RB; l++)
@@ -285,22 +299,23 @@ void build_tab_t(unsigned char *dst, const ts_ctx *ctx, const HostSlot &sl, cons
         }
         tb.QK[j] = z;
     }
-    std::memcpy(dst, &tb, sizeof(tb));
+    std::memcpy(dst, buf.data(), buf.size());
 }
 
-void build_tab(unsigned char *dst, const ts_ctx *ctx, int TB, const HostSlot &sl, const Group &g, int phase_k)
+void build_tab(unsigned char *dst, const ts_ctx *ctx, int TB, const HostSlot &sl, const Group &g, const IOLayout &io,
+               int phase_k)
 {
     if (ctx->prec == TS_C64) {
         switch (TB) {
-        case 12: return build_tab_t<float, 12, 5>(dst, ctx, sl, g, phase_k);
-        case 13: return build_tab_t<float, 13, 5>(dst, ctx, sl, g, phase_k);
-        default: return build_tab_t<float, 14, 5>(dst, ctx, sl, g, phase_k);
+        case 12: return build_tab_t<float, 12, 5>(dst, ctx, sl, g, io, phase_k);
+        case 13: return build_tab_t<float, 13, 5>(dst, ctx, sl, g, io, phase_k);
+        default: return build_tab_t<float, 14, 5>(dst, ctx, sl, g, io, phase_k);
         }
     }
     switch (TB) {
-    case 11: return build_tab_t<double, 11, 4>(dst, ctx, sl, g, phase_k);
-    case 12: return build_tab_t<double, 12, 4>(dst, ctx, sl, g, phase_k);
-    default: return build_tab_t<double, 13, 4>(dst, ctx, sl, g, phase_k);
+    case 11: return build_tab_t<double, 11, 4>(dst, ctx, sl, g, io, phase_k);
+    case 12: return build_tab_t<double, 12, 4>(dst, ctx, sl, g, io, phase_k);
+    default: return build_tab_t<double, 13, 4>(dst, ctx, sl, g, io, phase_k);
     }
 }
 
@@ -727,9 +742,9 @@ ts_status prepare_fused(ts_ctx *ctx, Schedule &S)
         seen[key] = idx;
         p.tab = idx;
         S.tabs.resize((size_t)(idx + 1) * S.tab_size);
-        build_tab(S.tabs.data() + (size_t)idx * S.tab_size, ctx, TB, sl, S.groups[p.group], p.phase_k);
+        build_tab(S.tabs.data() + (size_t)idx * S.tab_size, ctx, TB, sl, S.groups[p.group], S.io[p.group], p.phase_k);
     }
-    // frame angles: one table of 2^(N - tile bits) values per distinct (slot, group)
+    // frame terms: per distinct (slot, group), one angle and TB fields per tile
     struct ThetaJob {
         const HostSlot *sl;
         int group;
@@ -754,17 +769,20 @@ ts_status prepare_fused(ts_ctx *ctx, Schedule &S)
         jobs.push_back({&sl, p.group, ntheta});
         ntheta += (size_t)1 << (ctx->N - (g.c + g.h));
     }
-    if (S.tabs.size() > S.dtab_cap || ntheta > S.dtheta_cap) {
+    const size_t rsize = ctx->prec == TS_C64 ? sizeof(float) : sizeof(double);
+    const size_t frame_bytes = ntheta * (sizeof(double) + (size_t)TB * rsize);
+    if (S.tabs.size() > S.dtab_cap || frame_bytes > S.dtheta_cap) {
         release_tables(S, ctx->stream);
         if (!S.tabs.empty()) {
             TS_CUDA(ctx, cudaMalloc(&S.dtab, S.tabs.size()));
             S.dtab_cap = S.tabs.size();
         }
-        if (ntheta) {
-            TS_CUDA(ctx, cudaMalloc(&S.dtheta, ntheta * sizeof(double)));
-            S.dtheta_cap = ntheta;
+        if (frame_bytes) {
+            TS_CUDA(ctx, cudaMalloc(&S.dtheta, frame_bytes));
+            S.dtheta_cap = frame_bytes;
         }
     }
+    S.dgfield = S.dtheta ? static_cast<void *>(S.dtheta + ntheta) : nullptr;
     if (!S.tabs.empty())
         TS_CUDA(ctx, cudaMemcpyAsync(S.dtab, S.tabs.data(), S.tabs.size(), cudaMemcpyHostToDevice, ctx->stream));
     for (const auto &j : jobs) {
@@ -772,15 +790,30 @@ ts_status prepare_fused(ts_ctx *ctx, Schedule &S)
         const int N = ctx->N;
         const uint64_t nframes = UINT64_C(1) << (N - (g.c + g.h));
         const unsigned blocks = (unsigned)std::min<uint64_t>((nframes + 127) / 128, (uint64_t)ctx->sms * 8);
-        k_frame_theta<<<blocks, 128, 0, ctx->stream>>>(ctx->dJq + (size_t)j.sl->alpha * N * N,
-                                                       ctx->dhh + (size_t)j.sl->alpha * N, N, g.c, g.w, g.h,
-                                                       j.sl->t, j.sl->th0, nframes, S.dtheta + j.off);
+        const double *Jq = ctx->dJq + (size_t)j.sl->alpha * N * N;
+        const double *hh = ctx->dhh + (size_t)j.sl->alpha * N;
+        if (ctx->prec == TS_C64)
+            k_frame_terms<float><<<blocks, 128, 0, ctx->stream>>>(Jq, hh, N, g.c, g.w, g.h, j.sl->t, j.sl->th0, 1.0,
+                                                                  nframes, S.dtheta + j.off,
+                                                                  static_cast<float *>(S.dgfield) + j.off * TB);
+        else
+            k_frame_terms<double><<<blocks, 128, 0, ctx->stream>>>(Jq, hh, N, g.c, g.w, g.h, j.sl->t, j.sl->th0,
+                                                                   1.0 / M_PI, nframes, S.dtheta + j.off,
+                                                                   static_cast<double *>(S.dgfield) + j.off * TB);
         ctx->launches++;
         TS_CUDA(ctx, cudaGetLastError());
     }
     // the host image must stay valid until the copy is done
     TS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return TS_OK;
+}
+
+// Fields of the first frame of a (slot, group) whose angles start at frame offset off.
+const void *gfield_at(const ts_ctx *ctx, const Schedule &S, size_t off)
+{
+    if (ctx->prec == TS_C64)
+        return static_cast<const float *>(S.dgfield) + off * ctx->TB;
+    return static_cast<const double *>(S.dgfield) + off * ctx->TB;
 }
 
 ts_status run_fused(ts_ctx *ctx, void *buf, const Schedule &S)
@@ -803,6 +836,7 @@ ts_status run_fused(ts_ctx *ctx, void *buf, const Schedule &S)
         a.io = S.io[p.group];
         a.ham = hd;
         a.theta = p.slot >= 0 ? S.dtheta + p.theta_off : nullptr;
+        a.gfield = p.slot >= 0 ? gfield_at(ctx, S, p.theta_off) : nullptr;
         const uint64_t nblk = UINT64_C(1) << (ctx->N - (g.c + g.h));
         cudaError_t e = launch_tile(ctx, ctx->TB, buf, a, S.dtab, nblk);
         ctx->launches++;
@@ -834,7 +868,7 @@ ts_status run_slots(ts_ctx *ctx, Schedule &S, void *buf, int order, double tau, 
             void *keep = S.dtab;
             const size_t keep_cap = S.dtab_cap;
             double *keep_th = S.dtheta;
-            const size_t keep_th_cap = S.dtheta_cap;
+            const size_t keep_th_cap = S.dtheta_cap;  // (dgfield is re-derived by prepare_fused)
             S = Schedule();
             S.dtab = keep;
             S.dtab_cap = keep_cap;
@@ -899,6 +933,21 @@ ts_status sum_sz(ts_ctx *ctx, const void *buf, double *norm_and_p /* N+1 */)
     ctx->launches++;
     TS_CUDA(ctx, cudaGetLastError());
     return finish_sum(ctx, (int)nb, K, norm_and_p);
+}
+
+ts_status sum_norm(ts_ctx *ctx, const void *buf, double *out)
+{
+    const unsigned nb = red_blocks(ctx, 256 * 32);
+    ts_status st = ensure_part(ctx, (size_t)nb + 1);
+    if (st)
+        return st;
+    if (ctx->prec == TS_C64)
+        k_sum_norm<float2><<<nb, 256, 0, ctx->stream>>>((const float2 *)buf, ctx->N, ctx->dpart);
+    else
+        k_sum_norm<double2><<<nb, 256, 0, ctx->stream>>>((const double2 *)buf, ctx->N, ctx->dpart);
+    ctx->launches++;
+    TS_CUDA(ctx, cudaGetLastError());
+    return finish_sum(ctx, (int)nb, 1, out);
 }
 
 ts_status sum_diag(ts_ctx *ctx, const void *buf, int alpha, double *out)
@@ -1165,13 +1214,8 @@ ts_status ts_observe(ts_ctx *ctx, int what, double *out)
     const int N = ctx->N;
     ts_status st = TS_OK;
     switch (what) {
-    case TS_NORM: {
-        std::vector<double> v(N + 1);
-        st = sum_sz(ctx, ctx->psi.p, v.data());
-        if (!st)
-            out[0] = v[0];
-        return st;
-    }
+    case TS_NORM:
+        return sum_norm(ctx, ctx->psi.p, out);
     case TS_SZ: {
         std::vector<double> v(N + 1);
         st = sum_sz(ctx, ctx->psi.p, v.data());
@@ -1480,6 +1524,7 @@ ts_status batch_prepare(ts_batch *b, double tau, int64_t n)
             a.io = S.io[hp.group];
             a.ham = ham_dev(c);
             a.theta = hp.slot >= 0 ? S.dtheta + hp.theta_off : nullptr;
+            a.gfield = hp.slot >= 0 ? gfield_at(c, S, hp.theta_off) : nullptr;
             start += (uint32_t)((uint64_t)b->nstates[s] << bs.tile_shift);
         }
         b->blocks[p] = start;

@@ -42,16 +42,16 @@ __host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 __host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 
-// a * i^k, exact (swap and sign changes only)
+// a * i^k, exact (swap and sign changes only), branch-free: k is often different
+// in the lanes of a warp
 template <typename C> __host__ __device__ __forceinline__ C cmul_ipow(C a, int k)
 {
-    C r = a;
-    switch (k & 3) {
-    case 1: r.x = -a.y; r.y = a.x; break;
-    case 2: r.x = -a.x; r.y = -a.y; break;
-    case 3: r.x = a.y; r.y = -a.x; break;
-    default: break;
-    }
+    const bool sw = (k & 1) != 0, ng = (k & 2) != 0;
+    const auto x = sw ? -a.y : a.x;   // times i: (x, y) -> (-y, x)
+    const auto y = sw ? a.x : a.y;
+    C r;
+    r.x = ng ? -x : x;                // times -1
+    r.y = ng ? -y : y;
     return r;
 }
 

@@ -87,26 +87,21 @@ struct StepDesc {
 
 constexpr int kMaxSteps = 16;
 
-// Most spins outside a tile: N <= 34 and tiles of at least 11 spins.
-constexpr int kMaxFrame = 24;
-
 // Per-(slot, tile geometry, register chunk) tables, built on the host in FP64 and
 // rounded to R.  Angle unit: radians for complex64, half-turns for complex128.
-//   A[l*TB+m]   = t J^a_{pos l, pos m} / 4 for the tile's local bits (symmetric)
-//   QK[j]       c64:  (q(j), 0) with q(j) = sum_{l<m in chunk} A_lm s_l s_m
+// With A_lm = t J^a_{pos l, pos m} / 4 on the tile's local bits, W the register
+// window of the layout that applies the slot, and s = +-1 the local bits of thread
+// `tid`'s base index in that layout (its thread bits; the register bits are 0):
+//   TP[tid]     = sum over thread-bit pairs m < l of A_ml s_m s_l
+//   TC[b][tid]  = sum over thread bits m of A_{W+b, m} s_m        (b < RB)
+//   QK[j]       c64:  (q(j), 0) with q(j) = sum over register-bit pairs l < m of A s_l s_m
 //               c128: exp(-i q(j)) i^{pcq popcount(j)}
-//   G0[l]       = t h^a_{pos l} / 2
-//   GF[l*kMaxFrame+m] = t J^a_{pos l, fpos m} / 4, for the nf spins outside the
-//               tile (global positions fpos[m], increasing)
-// so that the field on tile spin l from the fixed spins of frame f is
-//   g_l(f) = G0[l] + sum_m GF[l][m] sigma_{fpos m}(f).
+// The per-frame terms (the frame angle and the fields on the tile spins) are
+// computed on the device once per schedule (k_frame_terms in ts4_tile.cuh).
 template <typename R, int TB, int RB> struct PassTab {
-    R A[TB * TB];
+    R TP[1 << (TB - RB)];
+    R TC[RB][1 << (TB - RB)];
     typename CT<R>::T QK[1 << RB];
-    R G0[TB];
-    R GF[TB * kMaxFrame];
-    int fpos[kMaxFrame];
-    int nf;
 };
 
 template <int RB, typename C> __device__ __forceinline__ void wht_regs(C (&x)[1 << RB], int lo, int hi)
@@ -135,10 +130,10 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v)
 __device__ __forceinline__ double norm2(float2 a) { return (double)a.x * a.x + (double)a.y * a.y; }
 __device__ __forceinline__ double norm2(double2 a) { return a.x * a.x + a.y * a.y; }
 
-// Block sums of several FP64 values; results land in out[0..K) of block 0's thread 0 view.
-template <int K> __device__ void block_sum(double (&v)[K], double *__restrict__ dst)
+// Block sums of several values; the results land in dst[0..K) (shared memory).
+template <int K, typename T> __device__ void block_sum(T (&v)[K], T *__restrict__ dst)
 {
-    __shared__ double red[32][K];
+    __shared__ T red[32][K];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; k++)
@@ -151,7 +146,7 @@ template <int K> __device__ void block_sum(double (&v)[K], double *__restrict__ 
     if (wid == 0) {
 #pragma unroll
         for (int k = 0; k < K; k++) {
-            double s = (lane < nw) ? red[lane][k] : 0.0;
+            T s = (lane < nw) ? red[lane][k] : T(0);
             s = warp_sum(s);
             if (lane == 0)
                 dst[k] = s;
@@ -165,8 +160,7 @@ template <int K> __device__ void block_sum(double (&v)[K], double *__restrict__ 
 // complex64: squares and pairwise sums in FP32 (error <= 5 u of the thread's
 // total), converted once to FP64; complex128: FP64 throughout.
 template <typename C, typename A>
-__device__ __forceinline__ void thread_sums32(const C *__restrict__ p, int stride, int n, double &tot,
-                                              double (&low)[5])
+__device__ __forceinline__ void thread_sums32(const C *__restrict__ p, int stride, int n, A &tot, A (&low)[5])
 {
     A q[32];
 #pragma unroll
@@ -192,25 +186,28 @@ __device__ __forceinline__ void thread_sums32(const C *__restrict__ p, int strid
 #pragma unroll
             for (int i = 0; i < w; i++)
                 t[i] = t[i] + t[i + w];
-        low[b] = (double)t[0];
+        low[b] = t[0];
     }
 #pragma unroll
     for (int w = 16; w >= 1; w >>= 1)
 #pragma unroll
         for (int i = 0; i < w; i++)
             q[i] = q[i] + q[i + w];
-    tot = (double)q[0];
+    tot = q[0];
 }
 
 template <typename C> struct AccOf;
 template <> struct AccOf<float2> { using T = float; };
 template <> struct AccOf<double2> { using T = double; };
 
-// Per block: [0] = sum |psi|^2, [1..] = sum |psi_s|^2 bit_i(s) for i < N  (stride N+1)
+// Per block: [0] = sum |psi|^2, [1..] = sum |psi_s|^2 bit_i(s) for i < N  (stride N+1).
+// Each block iteration covers 2^13 consecutive amplitudes; its 14 sums are formed in
+// the precision of the amplitudes (complex64: FP32 pairwise per thread and across
+// the block, relative error ~1e-6 of that range's weight) and added to FP64 totals.
 template <typename C>
 __global__ void __launch_bounds__(256) k_sum_sz(const C *__restrict__ psi, int N, double *__restrict__ part)
 {
-    // each block iteration covers a contiguous range of 2^13 amplitudes (256 threads x 32)
+    using A = typename AccOf<C>::T;
     constexpr int LB = 5;
     const uint64_t dim = UINT64_C(1) << N;
     __shared__ double acc_sh[64];
@@ -222,35 +219,74 @@ __global__ void __launch_bounds__(256) k_sum_sz(const C *__restrict__ psi, int N
     // amplitude base + (j << 8) + tid: thread bits are global bits 0..7 (coalesced),
     // the 32 per-thread values are global bits 8..12
     for (uint64_t base = (uint64_t)blockIdx.x * per_block; base < dim; base += (uint64_t)gridDim.x * per_block) {
-        double tot = 0.0, low[LB] = {0, 0, 0, 0, 0};
+        A tot = A(0), low[LB] = {A(0), A(0), A(0), A(0), A(0)};
         const uint64_t s0 = base + threadIdx.x;
         if (s0 < dim) {
             const uint64_t rem = (dim - s0 + 255) >> 8;       // elements s0 + 256 j below dim
             const int n = rem < 32 ? (int)rem : 32;
-            thread_sums32<C, typename AccOf<C>::T>(psi + s0, 256, n, tot, low);
+            thread_sums32<C, A>(psi + s0, 256, n, tot, low);
         }
-        double v[1 + 8 + LB];
+        A v[1 + 8 + LB];
         v[0] = tot;
 #pragma unroll
         for (int b = 0; b < 8; b++)
-            v[1 + b] = ((threadIdx.x >> b) & 1) ? tot : 0.0;
+            v[1 + b] = ((threadIdx.x >> b) & 1) ? tot : A(0);
 #pragma unroll
         for (int b = 0; b < LB; b++)
             v[1 + 8 + b] = low[b];
-        __shared__ double bs[1 + 8 + LB];
+        __shared__ A bs[1 + 8 + LB];
         block_sum<1 + 8 + LB>(v, bs);
         if (threadIdx.x == 0) {
-            acc_sh[0] += bs[0];
+            acc_sh[0] += (double)bs[0];
             for (int i = 0; i < N && i < RBITS; i++)
-                acc_sh[1 + i] += bs[1 + i];
+                acc_sh[1 + i] += (double)bs[1 + i];
             for (int i = RBITS; i < N; i++)
                 if ((base >> i) & 1)
-                    acc_sh[1 + i] += bs[0];
+                    acc_sh[1 + i] += (double)bs[0];
         }
         __syncthreads();
     }
     for (int i = threadIdx.x; i <= N; i += blockDim.x)
         part[(size_t)blockIdx.x * (N + 1) + i] = acc_sh[i];
+}
+
+// Per block: sum |psi|^2 over a grid-stride range; per thread FP32 (complex64) pairwise
+// sums of 32 amplitudes added to an FP64 running total, one FP64 block reduction.
+template <typename C>
+__global__ void __launch_bounds__(256) k_sum_norm(const C *__restrict__ psi, int N, double *__restrict__ part)
+{
+    using A = typename AccOf<C>::T;
+    const uint64_t dim = UINT64_C(1) << N;
+    const uint64_t per_block = (uint64_t)blockDim.x << 5;
+    double run = 0.0;
+    for (uint64_t base = (uint64_t)blockIdx.x * per_block; base < dim; base += (uint64_t)gridDim.x * per_block) {
+        const uint64_t s0 = base + threadIdx.x;
+        if (s0 < dim) {
+            const uint64_t rem = (dim - s0 + 255) >> 8;
+            const int n = rem < 32 ? (int)rem : 32;
+            A q[32];
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+                C a;
+                a.x = 0;
+                a.y = 0;
+                if (j < n)
+                    a = psi[s0 + (size_t)j * 256];
+                q[j] = (A)a.x * (A)a.x + (A)a.y * (A)a.y;
+            }
+#pragma unroll
+            for (int w = 16; w >= 1; w >>= 1)
+#pragma unroll
+                for (int i = 0; i < w; i++)
+                    q[i] = q[i] + q[i + w];
+            run += (double)q[0];
+        }
+    }
+    double v[1] = {run};
+    __shared__ double bs[1];
+    block_sum<1>(v, bs);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = bs[0];
 }
 
 // Per block: sum |psi_s|^2 * E_alpha(s) * wscale

@@ -87,16 +87,23 @@ struct TileArgs {
     int exact_sincos;   // c64 per-amplitude factor: 0 if |y| <= 0.05, 1 if |y| <= 0.5, 2 otherwise (sincospif)
     IOLayout io;
     HamDev ham;
-    const double *theta; // per frame f: t E_FF(f) + th0 in half-turns, reduced to [-1, 1] (k_frame_theta)
+    const double *theta; // per frame f: (t E_FF(f) + th0) / pi reduced to [-1, 1]  (k_frame_terms)
+    const void *gfield;  // per frame f: g_l(f) for the TB tile spins, R precision  (k_frame_terms)
 };
 
-// The frame part of a slot's angle, one value per tile f of a geometry (c, w, h):
-// theta[f] = (t E_FF(f) + th0) / pi reduced mod 2, where E_FF collects the field and
-// coupling terms among the spins outside the tile.  FP64, computed once per
-// schedule; the passes read one value per block.
-__global__ void k_frame_theta(const double *__restrict__ Jq, const double *__restrict__ hh, int N, int c, int w,
-                              int h, double t, double th0, uint64_t nframes, double *__restrict__ theta)
+// The frame-dependent parts of a slot's angle, for every tile f of a geometry
+// (c, w, h) with TB = c + h local spins (local bit l is global spin pos(l)):
+//   theta[f]       = (t E_FF(f) + th0) / pi reduced mod 2, E_FF = the field and
+//                    coupling terms among the spins outside the tile;
+//   g[f * TB + l]  = t (h_{pos l} / 2 + sum_{m outside} J_{pos l, m} sigma_m(f) / 4) * unit
+//                    (unit = 1 for radians, 1/pi for half-turns).
+// FP64 throughout, once per schedule; a pass reads TB + 2 words per block.
+template <typename R>
+__global__ void k_frame_terms(const double *__restrict__ Jq, const double *__restrict__ hh, int N, int c, int w,
+                              int h, double t, double th0, double unit, uint64_t nframes, double *__restrict__ theta,
+                              R *__restrict__ g)
 {
+    const int TB = c + h;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nframes; f += stride) {
         const uint64_t gb = tile_global_index(c, w, h, f, 0);
@@ -111,6 +118,14 @@ __global__ void k_frame_theta(const double *__restrict__ Jq, const double *__res
             acc += (((gb >> i) & 1) ? 1.0 : -1.0) * r;
         }
         theta[f] = halfturns_2pi(t * acc + th0);
+        for (int l = 0; l < TB; l++) {
+            const int i = l < h ? w + l : l - h;
+            double r = hh[i];
+            for (int m = 0; m < N; m++)
+                if (!in_tile(m, c, w, h))
+                    r += Jq[i * N + m] * (((gb >> m) & 1) ? 1.0 : -1.0);
+            g[f * TB + l] = (R)(t * r * unit);
+        }
     }
 }
 
@@ -171,7 +186,6 @@ template <int NT> struct SlotSoA128 {
 template <typename R, int TB, int RB> struct TileShared {
     // per-thread slot factors, computed before the tile occupies the registers
     typename std::conditional<sizeof(R) == 4, SlotSoA64<1 << (TB - RB)>, SlotSoA128<1 << (TB - RB)>>::type th_f;
-    R A[TB * TB];
     R g[TB];
     typename CT<R>::T Q[1 << RB];
     float th_hi, th_lo;  // c64: block angle in half-turns as a float pair
@@ -187,21 +201,28 @@ __device__ __forceinline__ float2 two_sum(float a, float b)
     return make_float2(s, err);
 }
 
-// e^{-iy} for |y| <= 0.5 from the Taylor series of cos and sin (truncation < 1e-12)
-__device__ __forceinline__ float2 cexpm_small(float y)
+// sin and cos of pi r for |r| <= 1/4 (plus rounding), without branches: x = pi r with
+// pi split into two floats (x to ~1e-15 relative), then the Taylor series of sin to
+// x^13 and of cos to x^14 (truncation below 3e-14 for |x| <= pi/4 + 1e-6).  The
+// caller removes the magnitude error of the rounded pair, so only the angle matters.
+__device__ __forceinline__ void sincos_quarter(float r, float &sn, float &cs)
 {
-    const float y2 = y * y;
-    float c = fmaf(y2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
-    c = fmaf(y2, c, -1.0f / 720.0f);
-    c = fmaf(y2, c, 1.0f / 24.0f);
-    c = fmaf(y2, c, -0.5f);
-    c = fmaf(y2, c, 1.0f);
-    float s = fmaf(y2, -1.0f / 39916800.0f, 1.0f / 362880.0f);
-    s = fmaf(y2, s, -1.0f / 5040.0f);
-    s = fmaf(y2, s, 1.0f / 120.0f);
-    s = fmaf(y2, s, -1.0f / 6.0f);
-    s = fmaf(y2, s, 1.0f);
-    return make_float2(c, -y * s);
+    const float pi_hi = 3.14159274101257324f, pi_lo = -8.74227766e-8f;   // pi = pi_hi + pi_lo
+    const float x = fmaf(r, pi_hi, r * pi_lo);
+    const float x2 = x * x;
+    float ps = fmaf(x2, 1.0f / 6227020800.0f, -1.0f / 39916800.0f);
+    ps = fmaf(x2, ps, 1.0f / 362880.0f);
+    ps = fmaf(x2, ps, -1.0f / 5040.0f);
+    ps = fmaf(x2, ps, 1.0f / 120.0f);
+    ps = fmaf(x2, ps, -1.0f / 6.0f);
+    sn = fmaf(x * x2, ps, x);
+    float pc = fmaf(x2, -1.0f / 87178291200.0f, 1.0f / 479001600.0f);
+    pc = fmaf(x2, pc, -1.0f / 3628800.0f);
+    pc = fmaf(x2, pc, 1.0f / 40320.0f);
+    pc = fmaf(x2, pc, -1.0f / 720.0f);
+    pc = fmaf(x2, pc, 1.0f / 24.0f);
+    pc = fmaf(x2, pc, -0.5f);
+    cs = fmaf(x2, pc, 1.0f);
 }
 
 __host__ __device__ constexpr int popc_c(int v) { return v ? (v & 1) + popc_c(v >> 1) : 0; }
@@ -218,37 +239,29 @@ __host__ __device__ constexpr int popc_c(int v) { return v ? (v & 1) + popc_c(v 
 // (compile-time W: only the thread's own bits enter the unrolled sums).
 template <int TB, int RB, int W>
 __device__ __forceinline__ void slot_thread_c64_w(SlotThreadC64 &o, uint32_t base, const TileShared<float, TB, RB> &sh,
-                                                  int pcq, float scale, float srel)
+                                                  int pcq, float scale, float srel, float tp, const float (&tc)[RB])
 {
     constexpr uint32_t chunk = ((1u << RB) - 1u) << W;
-    float sacc = 0.0f;
+    // the couplings among the thread's own bits (tp, tc) come from the pass table;
+    // the frame fields g_l depend on the block
+    float sacc = tp;
     float cb[RB];
 #pragma unroll
     for (int b = 0; b < RB; b++)
-        cb[b] = sh.g[W + b];
+        cb[b] = sh.g[W + b] + tc[b];
 #pragma unroll
     for (int m = 0; m < TB; m++) {
         if ((chunk >> m) & 1u)
             continue;
         const float sm = ((base >> m) & 1u) ? 1.0f : -1.0f;
         sacc = fmaf(sm, sh.g[m], sacc);
-#pragma unroll
-        for (int l = m + 1; l < TB; l++) {
-            if ((chunk >> l) & 1u)
-                continue;
-            const float sl = ((base >> l) & 1u) ? sm : -sm;
-            sacc = fmaf(sl, sh.A[m * TB + l], sacc);
-        }
-#pragma unroll
-        for (int b = 0; b < RB; b++)
-            cb[b] = fmaf(sm, sh.A[(W + b) * TB + m], cb[b]);
     }
     // thread angle in half-turns, reduced exactly: X = th_hi + th_lo + sacc / pi
     const float2 s1 = two_sum(sh.th_hi, sacc * 0.31830988618379067f);
     const float q = rintf(2.0f * s1.x);
     const float r = fmaf(-0.5f, q, s1.x) + (s1.y + sh.th_lo);
     float sn, cs;
-    sincospif(r, &sn, &cs);
+    sincos_quarter(r, sn, cs);
     const int kt = (pcq * (sh.pcF + __popc(base)) - (int)q) & 3;
     const float2 T = cmul_ipow(make_float2(cs * scale, -sn * scale), kt);
     // magnitude error d = cs^2 + sn^2 - 1 of the FP32 pair, to ~1e-14 (exact products by FMA;
@@ -281,13 +294,13 @@ __device__ __forceinline__ void slot_thread_c64_w(SlotThreadC64 &o, uint32_t bas
 template <int TB, int RB>
 __device__ __forceinline__ void slot_thread_c64(SlotThreadC64 &o, uint32_t base, int k,
                                                 const TileShared<float, TB, RB> &sh, int pcq, float scale,
-                                                float srel)
+                                                float srel, float tp, const float (&tc)[RB])
 {
     switch (k) {
-    case 0: slot_thread_c64_w<TB, RB, chunk_w<TB, RB>(0)>(o, base, sh, pcq, scale, srel); break;
-    case 1: slot_thread_c64_w<TB, RB, chunk_w<TB, RB>(1)>(o, base, sh, pcq, scale, srel); break;
-    case 2: slot_thread_c64_w<TB, RB, chunk_w<TB, RB>(2)>(o, base, sh, pcq, scale, srel); break;
-    default: slot_thread_c64_w<TB, RB, chunk_w<TB, RB>(3)>(o, base, sh, pcq, scale, srel); break;
+    case 0: slot_thread_c64_w<TB, RB, chunk_w<TB, RB>(0)>(o, base, sh, pcq, scale, srel, tp, tc); break;
+    case 1: slot_thread_c64_w<TB, RB, chunk_w<TB, RB>(1)>(o, base, sh, pcq, scale, srel, tp, tc); break;
+    case 2: slot_thread_c64_w<TB, RB, chunk_w<TB, RB>(2)>(o, base, sh, pcq, scale, srel, tp, tc); break;
+    default: slot_thread_c64_w<TB, RB, chunk_w<TB, RB>(3)>(o, base, sh, pcq, scale, srel, tp, tc); break;
     }
 }
 
@@ -362,28 +375,19 @@ __device__ __forceinline__ void slot_c64(float2 (&x)[1 << RB], const SlotSoA64<N
 // c128 slot: per-thread factors (errors ~1e-16; table of the in-chunk terms).
 template <int TB, int RB>
 __device__ __forceinline__ void slot_thread_c128(SlotThreadC128 &o, uint32_t base, int W,
-                                                 const TileShared<double, TB, RB> &sh, int pcq, double scale)
+                                                 const TileShared<double, TB, RB> &sh, int pcq, double scale,
+                                                 double tp, const double (&tc)[RB])
 {
-    double ang = sh.th;
+    double ang = sh.th + tp;
     double cb[RB];
 #pragma unroll
     for (int b = 0; b < RB; b++)
-        cb[b] = sh.g[W + b];
+        cb[b] = sh.g[W + b] + tc[b];
     const uint32_t chunk = ((1u << RB) - 1u) << W;
     for (int m = 0; m < TB; m++) {
         if ((chunk >> m) & 1u)
             continue;
-        const double sm = ((base >> m) & 1u) ? 1.0 : -1.0;
-        ang = fma(sm, sh.g[m], ang);
-        for (int l = m + 1; l < TB; l++) {
-            if ((chunk >> l) & 1u)
-                continue;
-            const double sl = ((base >> l) & 1u) ? sm : -sm;
-            ang = fma(sl, sh.A[m * TB + l], ang);
-        }
-#pragma unroll
-        for (int b = 0; b < RB; b++)
-            cb[b] = fma(sm, sh.A[(W + b) * TB + m], cb[b]);
+        ang = fma(((base >> m) & 1u) ? 1.0 : -1.0, sh.g[m], ang);
     }
     double2 eb = cexpm_pi(ang);
     eb.x *= scale;
@@ -480,6 +484,29 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
     const int c = a.c, w = a.w, h = a.h;
     const uint64_t gbase = tile_global_index(c, w, h, f, 0);
 
+    // ---- the slot's per-block terms and per-pass tables: a few words per thread,
+    // requested before the tile so that they do not queue behind its loads
+    static_assert(TB <= 32 && K::NT > 32, "prologue thread mapping");
+    R gv = R(0), tp = R(0), tc[RB];
+    double thv = 0.0;
+    C qv = C();
+#pragma unroll
+    for (int b = 0; b < RB; b++)
+        tc[b] = R(0);
+    if (a.has_slot) {
+        const TileTab<R, TB, RB> *tb = tabs + a.tab;
+        if (tid < TB)
+            gv = static_cast<const R *>(a.gfield)[f * TB + tid];
+        if (tid == 32)
+            thv = a.theta[f];
+        tp = tb->TP[tid];
+#pragma unroll
+        for (int b = 0; b < RB; b++)
+            tc[b] = tb->TC[b][tid];
+        if (tid < NR)
+            qv = tb->QK[tid];
+    }
+
     // ---- I/O layout: this thread's local base and its global offsets
     uint32_t base_io = 0;
 #pragma unroll
@@ -513,7 +540,7 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
         x[j] = __ldcs(psi + gi);
     }
 
-    // ---- per-block part of the slot: frame angle (precomputed, FP64) and fields g_l
+    // ---- per-block part of the slot into shared memory
     int pcq = 0;
     R scale = R(1);
     float srel = 0.0f;                 // exact scale / rounded scale - 1 (c64: sqrt 1/2 is not exact)
@@ -526,29 +553,16 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
         } else {
             scale = a.slot.scale;
         }
-        const TileTab<R, TB, RB> *tb = tabs + a.tab;
-        // field on each tile spin from the frame spins (table terms, R precision)
-        if (tid < TB) {
-            R acc = tb->G0[tid];
-            const int nf = tb->nf;
-#pragma unroll
-            for (int m = 0; m < kMaxFrame; m++)
-                if (m < nf) {
-                    const R v = tb->GF[tid * kMaxFrame + m];
-                    acc += ((gbase >> tb->fpos[m]) & 1) ? v : -v;
-                }
-            sh.g[tid] = acc;
-        } else if (tid == 32) {
-            const double th = a.theta[f];
-            sh.th = th;
-            sh.th_hi = (float)th;
-            sh.th_lo = (float)(th - (double)(float)th);
+        if (tid < TB)
+            sh.g[tid] = gv;
+        if (tid == 32) {
+            sh.th = thv;
+            sh.th_hi = (float)thv;
+            sh.th_lo = (float)(thv - (double)(float)thv);
             sh.pcF = __popcll(gbase);
         }
-        for (int k = tid; k < TB * TB; k += K::NT)
-            sh.A[k] = tb->A[k];
         if (tid < NR)
-            sh.Q[tid] = tb->QK[tid];
+            sh.Q[tid] = qv;
     }
     __syncthreads();
 
@@ -560,11 +574,11 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
                 kph = a.steps[s].k;
         if constexpr (sizeof(R) == 4) {
             SlotThreadC64 o;
-            slot_thread_c64<TB, RB>(o, base_of(kph), kph, sh, pcq, (float)scale, srel);
+            slot_thread_c64<TB, RB>(o, base_of(kph), kph, sh, pcq, (float)scale, srel, tp, tc);
             sh.th_f.put(tid, o);
         } else {
             SlotThreadC128 o;
-            slot_thread_c128<TB, RB>(o, base_of(kph), chunk_w<TB, RB>(kph), sh, pcq, (double)scale);
+            slot_thread_c128<TB, RB>(o, base_of(kph), chunk_w<TB, RB>(kph), sh, pcq, (double)scale, tp, tc);
             sh.th_f.put(tid, o);
         }
     }
