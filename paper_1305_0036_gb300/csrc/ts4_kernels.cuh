@@ -10,6 +10,8 @@
 
 #include "ts4_common.cuh"
 
+#include <utility>
+
 namespace ts4 {
 
 // ------------------------------------------------------------------ basic kernels
@@ -104,17 +106,24 @@ template <typename R, int TB, int RB> struct PassTab {
     typename CT<R>::T QK[1 << RB];
 };
 
+// Butterflies of register bit B on all 2^RB registers (register indices are template
+// constants: the compiler must not fall back to run-time indexing of the array).
+template <int B, typename C, int N, int... J>
+__device__ __forceinline__ void wht_bit(C (&x)[N], std::integer_sequence<int, J...>)
+{
+    ((void)((J & (1 << B)) ? 0 : (bfly(x[J], x[J | (1 << B)]), 0)), ...);
+}
+
+// Rotates register bits [lo, hi) (run-time range, uniform across the block).
+template <typename C, int N, int... B>
+__device__ __forceinline__ void wht_bits(C (&x)[N], int lo, int hi, std::integer_sequence<int, B...>)
+{
+    ((B >= lo && B < hi ? wht_bit<B>(x, std::make_integer_sequence<int, N>{}) : void()), ...);
+}
+
 template <int RB, typename C> __device__ __forceinline__ void wht_regs(C (&x)[1 << RB], int lo, int hi)
 {
-#pragma unroll
-    for (int b = 0; b < RB; b++) {
-        if (b >= lo && b < hi) {
-#pragma unroll
-            for (int j = 0; j < (1 << RB); j++)
-                if (!(j & (1 << b)))
-                    bfly(x[j], x[j | (1 << b)]);
-        }
-    }
+    wht_bits(x, lo, hi, std::make_integer_sequence<int, RB>{});
 }
 
 // ------------------------------------------------------------------ reductions (FP64)

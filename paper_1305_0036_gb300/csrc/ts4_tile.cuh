@@ -23,6 +23,8 @@
 // of two: every warp access is conflict-free.
 #pragma once
 
+#include <utility>
+
 #include "ts4_kernels.cuh"
 
 #include <type_traits>
@@ -193,11 +195,13 @@ template <typename R, int TB, int RB> struct TileShared {
     int pcF;
 };
 
+// Knuth's two-sum: s + err = a + b exactly.  Written with the _rn intrinsics, which the
+// compiler never fuses into multiply-adds, so the transform stays error-free.
 __device__ __forceinline__ float2 two_sum(float a, float b)
 {
-    const float s = a + b;
-    const float bb = s - a;
-    const float err = (a - (s - bb)) + (b - bb);
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
     return make_float2(s, err);
 }
 
@@ -257,7 +261,7 @@ __device__ __forceinline__ void slot_thread_c64_w(SlotThreadC64 &o, uint32_t bas
         sacc = fmaf(sm, sh.g[m], sacc);
     }
     // thread angle in half-turns, reduced exactly: X = th_hi + th_lo + sacc / pi
-    const float2 s1 = two_sum(sh.th_hi, sacc * 0.31830988618379067f);
+    const float2 s1 = two_sum(sh.th_hi, __fmul_rn(sacc, 0.31830988618379067f));
     const float q = rintf(2.0f * s1.x);
     const float r = fmaf(-0.5f, q, s1.x) + (s1.y + sh.th_lo);
     float sn, cs;
@@ -267,8 +271,8 @@ __device__ __forceinline__ void slot_thread_c64_w(SlotThreadC64 &o, uint32_t bas
     // magnitude error d = cs^2 + sn^2 - 1 of the FP32 pair, to ~1e-14 (exact products by FMA;
     // cs^2 in [1/2, 1] so cs^2 - 1 is exact); (1 - d/2) restores unit magnitude
     {
-        const float p1 = cs * cs, e1 = fmaf(cs, cs, -p1);
-        const float p2 = sn * sn, e2 = fmaf(sn, sn, -p2);
+        const float p1 = __fmul_rn(cs, cs), e1 = fmaf(cs, cs, -p1);
+        const float p2 = __fmul_rn(sn, sn), e2 = fmaf(sn, sn, -p2);
         const float d = ((p1 - 1.0f) + p2) + (e1 + e2);
         o.kT = fmaf(-0.5f, d, srel);
     }
@@ -344,20 +348,33 @@ template <int MODE> __device__ __forceinline__ void unit_factor(float y, float &
 // has unit magnitude to ~1e-10 times the exact scale (the dropped terms kT c and kT s of the
 // exact product (1 + kT)((1 + c) - i s) change it by < 2e-10); the FP32 roundings left are
 // those of products with x_j, which change from step to step and do not build up.
+// One amplitude, register index J (compile-time: every table index below is a constant).
+template <int MODE, int J, int NT>
+__device__ __forceinline__ void slot_c64_one(float2 &xj, const SlotSoA64<NT> &o, int t, const float2 *__restrict__ Q,
+                                             float kT)
+{
+    constexpr int P = popc_c(J);
+    const float y = (o.Lo[J & 7][t] + o.Hi[J >> 3][t]) + Q[J].x;
+    float c, s;
+    unit_factor<MODE>(y, c, s);
+    const float ct = c + kT;
+    const float2 x1 = cmul(xj, o.R[P][t]);
+    xj = make_float2(fmaf(x1.x, ct, fmaf(x1.y, s, x1.x)), fmaf(x1.y, ct, fmaf(-x1.x, s, x1.y)));
+}
+
+template <int MODE, int NT, int... J>
+__device__ __forceinline__ void slot_c64_apply_seq(float2 (&x)[sizeof...(J)], const SlotSoA64<NT> &o, int t,
+                                                   const float2 *__restrict__ Q, std::integer_sequence<int, J...>)
+{
+    const float kT = o.kT[t];
+    (slot_c64_one<MODE, J, NT>(x[J], o, t, Q, kT), ...);
+}
+
 template <int RB, int MODE, int NT>
 __device__ __forceinline__ void slot_c64_apply(float2 (&x)[1 << RB], const SlotSoA64<NT> &o, int t,
                                                const float2 *__restrict__ Q)
 {
-    const float kT = o.kT[t];
-#pragma unroll
-    for (int j = 0; j < (1 << RB); j++) {
-        const float y = (o.Lo[j & 7][t] + o.Hi[j >> 3][t]) + Q[j].x;
-        float c, s;
-        unit_factor<MODE>(y, c, s);
-        const float ct = c + kT;
-        const float2 x1 = cmul(x[j], o.R[popc_c(j)][t]);
-        x[j] = make_float2(fmaf(x1.x, ct, fmaf(x1.y, s, x1.x)), fmaf(x1.y, ct, fmaf(-x1.x, s, x1.y)));
-    }
+    slot_c64_apply_seq<MODE, NT>(x, o, t, Q, std::make_integer_sequence<int, (1 << RB)>{});
 }
 
 template <int RB, int NT>
@@ -413,13 +430,18 @@ __device__ __forceinline__ void slot_thread_c128(SlotThreadC128 &o, uint32_t bas
     o.fhi[3] = cmul(a1, b1);
 }
 
+template <int NT, int... J>
+__device__ __forceinline__ void slot_c128_seq(double2 (&x)[16], const SlotSoA128<NT> &o, int t,
+                                              const double2 *__restrict__ Q, std::integer_sequence<int, J...>)
+{
+    ((x[J] = cmul(x[J], cmul(cmul(o.flo[J & 3][t], o.fhi[J >> 2][t]), Q[J]))), ...);
+}
+
 template <int NT>
 __device__ __forceinline__ void slot_c128(double2 (&x)[16], const SlotSoA128<NT> &o, int t,
                                           const double2 *__restrict__ Q)
 {
-#pragma unroll
-    for (int j = 0; j < 16; j++)
-        x[j] = cmul(x[j], cmul(cmul(o.flo[j & 3][t], o.fhi[j >> 2][t]), Q[j]));
+    slot_c128_seq(x, o, t, Q, std::make_integer_sequence<int, 16>{});
 }
 
 template <typename R, int TB, int RB> struct TileKernel {
@@ -442,19 +464,52 @@ template <typename R, int TB, int RB> struct TileKernel {
         return b;
     }
 
-    template <int K> static __device__ __forceinline__ void store_chunk(C *sm, uint32_t pbase, const C (&x)[NR])
+    // register j of layout K lives at pbase + P(j << W): a compile-time offset per j
+    template <int K, int... J>
+    static __device__ __forceinline__ void store_seq(C *sm, uint32_t pbase, const C (&x)[NR],
+                                                     std::integer_sequence<int, J...>)
     {
         constexpr int W = chunk_w<TB, RB>(K);
+        ((sm[pbase + padidx<ES>((uint32_t)J << W)] = x[J]), ...);
+    }
+    template <int K, int... J>
+    static __device__ __forceinline__ void load_seq(const C *sm, uint32_t pbase, C (&x)[NR],
+                                                    std::integer_sequence<int, J...>)
+    {
+        constexpr int W = chunk_w<TB, RB>(K);
+        ((x[J] = sm[pbase + padidx<ES>((uint32_t)J << W)]), ...);
+    }
+    // global index of register J in the I/O layout: the thread's index with the bits of
+    // the register window (offsets gst[b]) that J sets
+    template <int J>
+    static __device__ __forceinline__ uint64_t gidx(uint64_t gthr, const uint64_t (&gst)[RB])
+    {
+        uint64_t gi = gthr;
 #pragma unroll
-        for (int j = 0; j < NR; j++)
-            sm[pbase + padidx<ES>((uint32_t)j << W)] = x[j];
+        for (int b = 0; b < RB; b++)
+            if ((J >> b) & 1)
+                gi |= gst[b];
+        return gi;
+    }
+    template <int... J>
+    static __device__ __forceinline__ void gload(const C *__restrict__ psi, uint64_t gthr, const uint64_t (&gst)[RB],
+                                                 C (&x)[NR], std::integer_sequence<int, J...>)
+    {
+        ((x[J] = __ldcs(psi + gidx<J>(gthr, gst))), ...);
+    }
+    template <int... J>
+    static __device__ __forceinline__ void gstore(C *__restrict__ psi, uint64_t gthr, const uint64_t (&gst)[RB],
+                                                  const C (&x)[NR], std::integer_sequence<int, J...>)
+    {
+        (__stcs(psi + gidx<J>(gthr, gst), x[J]), ...);
+    }
+    template <int K> static __device__ __forceinline__ void store_chunk(C *sm, uint32_t pbase, const C (&x)[NR])
+    {
+        store_seq<K>(sm, pbase, x, std::make_integer_sequence<int, NR>{});
     }
     template <int K> static __device__ __forceinline__ void load_chunk(const C *sm, uint32_t pbase, C (&x)[NR])
     {
-        constexpr int W = chunk_w<TB, RB>(K);
-#pragma unroll
-        for (int j = 0; j < NR; j++)
-            x[j] = sm[pbase + padidx<ES>((uint32_t)j << W)];
+        load_seq<K>(sm, pbase, x, std::make_integer_sequence<int, NR>{});
     }
 
     static __device__ __forceinline__ void apply_slot(C (&x)[NR], const TileShared<R, TB, RB> &sh, int mode)
@@ -530,15 +585,7 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
     auto base_of = [&](int k) { return k == 0 ? b0 : k == 1 ? b1 : k == 2 ? b2 : b3; };
     // ---- issue the tile's loads first: the slot set-up below runs under their latency
     C x[NR];
-#pragma unroll
-    for (int j = 0; j < NR; j++) {
-        uint64_t gi = gthr;
-#pragma unroll
-        for (int b = 0; b < RB; b++)
-            if ((j >> b) & 1)
-                gi |= gst[b];
-        x[j] = __ldcs(psi + gi);
-    }
+    K::gload(psi, gthr, gst, x, std::make_integer_sequence<int, NR>{});
 
     // ---- per-block part of the slot into shared memory
     int pcq = 0;
@@ -635,15 +682,7 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
 #pragma unroll
     for (int b = 0; b < RB; b++)
         asm volatile("mov.b64 %0, %0;" : "+l"(gst[b]));
-#pragma unroll
-    for (int j = 0; j < NR; j++) {
-        uint64_t gi = gthr;
-#pragma unroll
-        for (int b = 0; b < RB; b++)
-            if ((j >> b) & 1)
-                gi |= gst[b];
-        __stcs(psi + gi, x[j]);
-    }
+    K::gstore(psi, gthr, gst, x, std::make_integer_sequence<int, NR>{});
 }
 
 // Resident blocks per SM the register allocation is sized for: 64K registers hold

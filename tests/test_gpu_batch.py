@@ -75,6 +75,10 @@ def test_config4_ensemble_against_single_state_runs(ts4):
             single = c.get_state()
             np.testing.assert_allclose(c.sz(), szs[i][j], atol=1e-6)
             c.close()
-            # same kernels, same arithmetic: identical up to launch-independent rounding
-            assert np.linalg.norm(got[j].astype(np.complex128) - single) <= 1e-5
+            # Same formula in both runs, but the batched and the single-state kernels are
+            # compiled separately and the compiler may fuse a multiply and an add in one and
+            # not in the other.  Those roundings (<= 2^-24 relative, unbiased) add up like a
+            # random walk over the ~20 (N + 8) rounded operations per amplitude and step.
+            tol = 4.0 * np.sqrt(20 * cfg["nsteps"] * (s.N + 8)) * U32
+            assert np.linalg.norm(got[j].astype(np.complex128) - single) <= tol
     b.close()
