@@ -287,13 +287,16 @@ def run_ours(args, ws, rank, local):
     barrier(ws)
     t0 = time.perf_counter()
     ctx.set_state_host_ptr(host.data_ptr())
+    t_up = time.perf_counter()
     norm = 1.0
     for _ in range(args.steps):
         ctx.step(TAU, 1)
         norm = ctx.norm()
-    e2e_s = time.perf_counter() - t0
-    e2e_s = max_over_ranks(ws, e2e_s)
+    t1 = time.perf_counter()
+    e2e_s = max_over_ranks(ws, t1 - t0)
     e2e_value = ws * args.steps / e2e_s
+    e2e_upload_ms = 1000.0 * (t_up - t0)
+    e2e_step_ms = 1000.0 * (t1 - t_up) / args.steps
 
     line = {
         "metric": METRIC, "value": value, "unit": "TS4 steps/s", "n_gpus": ws, "steps": args.steps,
@@ -311,7 +314,8 @@ def run_ours(args, ws, rank, local):
                      "kernel": "k_tile", "alg_bytes_per_launch": alg_bytes_launch,
                      "avg_launch_ms": avg_pass_ms},
         "e2e": {"value": e2e_value, "unit": "TS4 steps/s", "h2d_bytes_per_step": state_bytes / args.steps,
-                "d2h_bytes_per_step": 8 * (N + 1), "final_norm": norm},
+                "d2h_bytes_per_step": 8, "final_norm": norm,
+                "upload_ms": e2e_upload_ms, "step_plus_norm_ms": e2e_step_ms},
         "gpu_launches": launches,
         "clocks": clk,
     }

@@ -134,11 +134,14 @@ __global__ void k_frame_terms(const double *__restrict__ Jq, const double *__res
 // Per-(slot, group) tables: PassTab (host-built in FP64, see ts4_kernels.cuh)
 template <typename R, int TB, int RB> using TileTab = PassTab<R, TB, RB>;
 
-struct SlotThreadC64 {
-    float2 R[6];      // T i^{pcq p}, p = popcount of the register index
-    float Lo[8];
+// Per-thread factors of a complex64 slot with 2^RB registers; the register index j splits
+// into its low RB - 2 bits (Lo) and its top 2 bits (Hi).
+template <int RB> struct SlotThreadC64 {
+    static constexpr int LB = RB - 2;
+    float2 R[RB + 1];  // T i^{pcq p}, p = popcount of the register index
+    float Lo[1 << LB];
     float Hi[4];
-    float kT;         // |T (1 + kT)| = |scale| to ~1e-14: the FP32 magnitude error of T, removed
+    float kT;          // |T (1 + kT)| = |scale| to ~1e-14: the FP32 magnitude error of T, removed
 };
 
 struct SlotThreadC128 {
@@ -150,19 +153,20 @@ struct SlotThreadC128 {
 // slot step, one array per field ([field][thread]), so that a warp reading one
 // field touches consecutive words: an array of the structs above (stride 104 or
 // 128 bytes) would put several lanes of a warp on the same bank.
-template <int NT> struct SlotSoA64 {
-    float2 R[6][NT];
-    float Lo[8][NT];
+template <int NT, int RB> struct SlotSoA64 {
+    static constexpr int LB = RB - 2;
+    float2 R[RB + 1][NT];
+    float Lo[1 << LB][NT];
     float Hi[4][NT];
     float kT[NT];
 
-    __device__ __forceinline__ void put(int t, const SlotThreadC64 &o)
+    __device__ __forceinline__ void put(int t, const SlotThreadC64<RB> &o)
     {
 #pragma unroll
-        for (int k = 0; k < 6; k++)
+        for (int k = 0; k <= RB; k++)
             R[k][t] = o.R[k];
 #pragma unroll
-        for (int k = 0; k < 8; k++)
+        for (int k = 0; k < (1 << LB); k++)
             Lo[k][t] = o.Lo[k];
 #pragma unroll
         for (int k = 0; k < 4; k++)
@@ -187,7 +191,7 @@ template <int NT> struct SlotSoA128 {
 
 template <typename R, int TB, int RB> struct TileShared {
     // per-thread slot factors, computed before the tile occupies the registers
-    typename std::conditional<sizeof(R) == 4, SlotSoA64<1 << (TB - RB)>, SlotSoA128<1 << (TB - RB)>>::type th_f;
+    typename std::conditional<sizeof(R) == 4, SlotSoA64<1 << (TB - RB), RB>, SlotSoA128<1 << (TB - RB)>>::type th_f;
     R g[TB];
     typename CT<R>::T Q[1 << RB];
     float th_hi, th_lo;  // c64: block angle in half-turns as a float pair
@@ -242,7 +246,7 @@ __host__ __device__ constexpr int popc_c(int v) { return v ? (v & 1) + popc_c(v 
 // Per-thread part, for the register window W of the layout that applies the slot
 // (compile-time W: only the thread's own bits enter the unrolled sums).
 template <int TB, int RB, int W>
-__device__ __forceinline__ void slot_thread_c64_w(SlotThreadC64 &o, uint32_t base, const TileShared<float, TB, RB> &sh,
+__device__ __forceinline__ void slot_thread_c64_w(SlotThreadC64<RB> &o, uint32_t base, const TileShared<float, TB, RB> &sh,
                                                   int pcq, float scale, float srel, float tp, const float (&tc)[RB])
 {
     constexpr uint32_t chunk = ((1u << RB) - 1u) << W;
@@ -280,23 +284,24 @@ __device__ __forceinline__ void slot_thread_c64_w(SlotThreadC64 &o, uint32_t bas
 #pragma unroll
     for (int p = 0; p <= RB; p++)
         o.R[p] = cmul_ipow(T, (pcq * p) & 3);
+    constexpr int LB = RB - 2;
     o.Lo[0] = 0.0f;
 #pragma unroll
-    for (int b = 0; b < 3; b++)
+    for (int b = 0; b < LB; b++)
 #pragma unroll
         for (int k = 0; k < (1 << b); k++) {
             const float v = o.Lo[k];
             o.Lo[k] = v - cb[b];
             o.Lo[k | (1 << b)] = v + cb[b];
         }
-    o.Hi[0] = -cb[3] - cb[4];
-    o.Hi[1] = cb[3] - cb[4];
-    o.Hi[2] = -cb[3] + cb[4];
-    o.Hi[3] = cb[3] + cb[4];
+    o.Hi[0] = -cb[LB] - cb[LB + 1];
+    o.Hi[1] = cb[LB] - cb[LB + 1];
+    o.Hi[2] = -cb[LB] + cb[LB + 1];
+    o.Hi[3] = cb[LB] + cb[LB + 1];
 }
 
 template <int TB, int RB>
-__device__ __forceinline__ void slot_thread_c64(SlotThreadC64 &o, uint32_t base, int k,
+__device__ __forceinline__ void slot_thread_c64(SlotThreadC64<RB> &o, uint32_t base, int k,
                                                 const TileShared<float, TB, RB> &sh, int pcq, float scale,
                                                 float srel, float tp, const float (&tc)[RB])
 {
@@ -349,12 +354,12 @@ template <int MODE> __device__ __forceinline__ void unit_factor(float y, float &
 // exact product (1 + kT)((1 + c) - i s) change it by < 2e-10); the FP32 roundings left are
 // those of products with x_j, which change from step to step and do not build up.
 // One amplitude, register index J (compile-time: every table index below is a constant).
-template <int MODE, int J, int NT>
-__device__ __forceinline__ void slot_c64_one(float2 &xj, const SlotSoA64<NT> &o, int t, const float2 *__restrict__ Q,
-                                             float kT)
+template <int MODE, int J, int NT, int RB>
+__device__ __forceinline__ void slot_c64_one(float2 &xj, const SlotSoA64<NT, RB> &o, int t,
+                                             const float2 *__restrict__ Q, float kT)
 {
-    constexpr int P = popc_c(J);
-    const float y = (o.Lo[J & 7][t] + o.Hi[J >> 3][t]) + Q[J].x;
+    constexpr int P = popc_c(J), LB = RB - 2;
+    const float y = (o.Lo[J & ((1 << LB) - 1)][t] + o.Hi[J >> LB][t]) + Q[J].x;
     float c, s;
     unit_factor<MODE>(y, c, s);
     const float ct = c + kT;
@@ -362,23 +367,23 @@ __device__ __forceinline__ void slot_c64_one(float2 &xj, const SlotSoA64<NT> &o,
     xj = make_float2(fmaf(x1.x, ct, fmaf(x1.y, s, x1.x)), fmaf(x1.y, ct, fmaf(-x1.x, s, x1.y)));
 }
 
-template <int MODE, int NT, int... J>
-__device__ __forceinline__ void slot_c64_apply_seq(float2 (&x)[sizeof...(J)], const SlotSoA64<NT> &o, int t,
+template <int MODE, int NT, int RB, int... J>
+__device__ __forceinline__ void slot_c64_apply_seq(float2 (&x)[sizeof...(J)], const SlotSoA64<NT, RB> &o, int t,
                                                    const float2 *__restrict__ Q, std::integer_sequence<int, J...>)
 {
     const float kT = o.kT[t];
-    (slot_c64_one<MODE, J, NT>(x[J], o, t, Q, kT), ...);
+    (slot_c64_one<MODE, J, NT, RB>(x[J], o, t, Q, kT), ...);
 }
 
 template <int RB, int MODE, int NT>
-__device__ __forceinline__ void slot_c64_apply(float2 (&x)[1 << RB], const SlotSoA64<NT> &o, int t,
+__device__ __forceinline__ void slot_c64_apply(float2 (&x)[1 << RB], const SlotSoA64<NT, RB> &o, int t,
                                                const float2 *__restrict__ Q)
 {
-    slot_c64_apply_seq<MODE, NT>(x, o, t, Q, std::make_integer_sequence<int, (1 << RB)>{});
+    slot_c64_apply_seq<MODE, NT, RB>(x, o, t, Q, std::make_integer_sequence<int, (1 << RB)>{});
 }
 
 template <int RB, int NT>
-__device__ __forceinline__ void slot_c64(float2 (&x)[1 << RB], const SlotSoA64<NT> &o, int t,
+__device__ __forceinline__ void slot_c64(float2 (&x)[1 << RB], const SlotSoA64<NT, RB> &o, int t,
                                          const float2 *__restrict__ Q, int mode)
 {
     if (mode == 0)
@@ -503,6 +508,29 @@ template <typename R, int TB, int RB> struct TileKernel {
     {
         (__stcs(psi + gidx<J>(gthr, gst), x[J]), ...);
     }
+    // the same with 32-bit element offsets from the thread's base pointer (states of at
+    // most 2^32 amplitudes): one integer add tree and one wide multiply-add per address
+    template <int J> static __device__ __forceinline__ uint32_t goff32(const uint32_t (&gst)[RB])
+    {
+        uint32_t o = 0;
+#pragma unroll
+        for (int b = 0; b < RB; b++)
+            if ((J >> b) & 1)
+                o += gst[b];
+        return o;
+    }
+    template <int... J>
+    static __device__ __forceinline__ void gload32(const C *__restrict__ p, const uint32_t (&gst)[RB], C (&x)[NR],
+                                                   std::integer_sequence<int, J...>)
+    {
+        ((x[J] = __ldcs(p + goff32<J>(gst))), ...);
+    }
+    template <int... J>
+    static __device__ __forceinline__ void gstore32(C *__restrict__ p, const uint32_t (&gst)[RB], const C (&x)[NR],
+                                                    std::integer_sequence<int, J...>)
+    {
+        (__stcs(p + goff32<J>(gst), x[J]), ...);
+    }
     template <int K> static __device__ __forceinline__ void store_chunk(C *sm, uint32_t pbase, const C (&x)[NR])
     {
         store_seq<K>(sm, pbase, x, std::make_integer_sequence<int, NR>{});
@@ -584,8 +612,16 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
     const uint32_t b3 = (K::NCH > 3) ? K::template chunk_base<3>(tid) : 0u;
     auto base_of = [&](int k) { return k == 0 ? b0 : k == 1 ? b1 : k == 2 ? b2 : b3; };
     // ---- issue the tile's loads first: the slot set-up below runs under their latency
+    const bool narrow = a.ham.N <= 32;   // element offsets of the register window fit in 32 bits
+    uint32_t gst32[RB];
+#pragma unroll
+    for (int b = 0; b < RB; b++)
+        gst32[b] = (uint32_t)gst[b];
     C x[NR];
-    K::gload(psi, gthr, gst, x, std::make_integer_sequence<int, NR>{});
+    if (narrow)
+        K::gload32(psi + gthr, gst32, x, std::make_integer_sequence<int, NR>{});
+    else
+        K::gload(psi, gthr, gst, x, std::make_integer_sequence<int, NR>{});
 
     // ---- per-block part of the slot into shared memory
     int pcq = 0;
@@ -620,7 +656,7 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
             if (a.steps[s].ph)
                 kph = a.steps[s].k;
         if constexpr (sizeof(R) == 4) {
-            SlotThreadC64 o;
+            SlotThreadC64<RB> o;
             slot_thread_c64<TB, RB>(o, base_of(kph), kph, sh, pcq, (float)scale, srel, tp, tc);
             sh.th_f.put(tid, o);
         } else {
@@ -679,21 +715,32 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
     // (opaque copies: keeps the compiler from holding the 2^RB load addresses live
     // across the whole pass)
     asm volatile("mov.b64 %0, %0;" : "+l"(gthr));
+    if (narrow) {
 #pragma unroll
-    for (int b = 0; b < RB; b++)
-        asm volatile("mov.b64 %0, %0;" : "+l"(gst[b]));
-    K::gstore(psi, gthr, gst, x, std::make_integer_sequence<int, NR>{});
+        for (int b = 0; b < RB; b++)
+            asm volatile("mov.b32 %0, %0;" : "+r"(gst32[b]));
+        K::gstore32(psi + gthr, gst32, x, std::make_integer_sequence<int, NR>{});
+    } else {
+#pragma unroll
+        for (int b = 0; b < RB; b++)
+            asm volatile("mov.b64 %0, %0;" : "+l"(gst[b]));
+        K::gstore(psi, gthr, gst, x, std::make_integer_sequence<int, NR>{});
+    }
 }
 
-// Resident blocks per SM the register allocation is sized for: 64K registers hold
-// 2 blocks of 256 threads or 4 blocks of 128 threads at 128 registers each.
-__host__ __device__ constexpr int tile_min_blocks(int thread_bits)
+// Resident blocks per SM the register allocation is sized for: about twice the tile's
+// registers per thread, i.e. 4 blocks of 128 threads (c64, 32 amplitudes, 128 registers),
+// 4 blocks of 256 threads (c64, 16 amplitudes, 64 registers), 2 blocks of 256 threads
+// (c128, 16 amplitudes, 128 registers), ... within the SM's 64K registers.
+__host__ __device__ constexpr int tile_min_blocks(int thread_bits, int reg_elems)
 {
-    return thread_bits <= 7 ? 4 : (thread_bits <= 8 ? 2 : 1);
+    // 2^RB amplitudes per thread take reg_elems = 2^RB x (8 or 16 bytes) / 4 registers;
+    // budget about twice that per thread
+    return (65536 / (2 * reg_elems)) >> thread_bits > 0 ? (65536 / (2 * reg_elems)) >> thread_bits : 1;
 }
 
 template <typename R, int TB, int RB>
-__global__ void __launch_bounds__(1 << (TB - RB), tile_min_blocks(TB - RB))
+__global__ void __launch_bounds__(1 << (TB - RB), tile_min_blocks(TB - RB, (int)(sizeof(typename CT<R>::T) / 4) << RB))
 k_tile(typename CT<R>::T *__restrict__ psi, const __grid_constant__ TileArgs a,
        const TileTab<R, TB, RB> *__restrict__ tabs)
 {
@@ -714,7 +761,7 @@ struct BatchSys {
 };
 
 template <typename R, int TB, int RB>
-__global__ void __launch_bounds__(1 << (TB - RB), tile_min_blocks(TB - RB))
+__global__ void __launch_bounds__(1 << (TB - RB), tile_min_blocks(TB - RB, (int)(sizeof(typename CT<R>::T) / 4) << RB))
 k_tile_batch(const BatchSys *__restrict__ sys, const TileArgs *__restrict__ args, int nsys)
 {
     const uint32_t b = blockIdx.x;
