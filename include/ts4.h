@@ -81,7 +81,17 @@ enum {
     TS_SZ = 3,     /* <S^z_j> for j = 1..N                               -> N doubles */
     TS_ECHO = 4,   /* Loschmidt echo |<psi_0|psi>|^2 (Eq. 11, Sigma = 0)
                       against the reference saved by ts_save_reference   -> 1 double */
-    TS_OVERLAP = 5 /* <psi_0|psi> as (re, im)                            -> 2 doubles */
+    TS_OVERLAP = 5, /* <psi_0|psi> as (re, im)                           -> 2 doubles */
+    /* Two-spin correlations <S^a_i S^a_j> for all i, j (the paper measures local
+     * polarisations and the echo, Sec. 4.2; these extend them to correlation
+     * functions).  Row-major N x N, symmetric, diagonal = norm / 4.  The x and y
+     * cases rotate a scratch copy of the state into the a eigenbasis (one
+     * Walsh-Hadamard layer with diagonal phases, as for TS_ENERGY). */
+    TS_SZSZ = 6,   /* <S^z_i S^z_j>                                      -> N*N doubles */
+    TS_SXSX = 7,   /* <S^x_i S^x_j>                                      -> N*N doubles */
+    TS_SYSY = 8,   /* <S^y_i S^y_j>                                      -> N*N doubles */
+    TS_SX = 9,     /* <S^x_j> for j = 1..N                               -> N doubles */
+    TS_SY = 10     /* <S^y_j> for j = 1..N                               -> N doubles */
 };
 
 /* Kernels for the rotation layers (ts_set_schedule). */

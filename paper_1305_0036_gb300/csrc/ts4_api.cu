@@ -112,6 +112,8 @@ void reset_schedule(Schedule &S, cudaStream_t st)
 }
 
 constexpr int kMaxN = 34;
+// largest host read-back of one reduction: the joint bit weights of k_sum_pairs
+constexpr int kMaxOut = 1 + kMaxN + kMaxN * (kMaxN - 1) / 2;
 
 } // namespace
 
@@ -130,7 +132,7 @@ struct ts_ctx {
     bool ref_valid = false;
     double *dpart = nullptr;
     size_t part_cap = 0;      // doubles
-    double *hout = nullptr;   // pinned, kMaxN + 8 doubles
+    double *hout = nullptr;   // pinned, kMaxOut doubles
     int kernel = TS_KERNEL_FUSED;
     int TB = 0, RB = 0, cbits = 0;
     Schedule sched;       // last ts_step schedule
@@ -899,6 +901,8 @@ ts_status run_slots(ts_ctx *ctx, Schedule &S, void *buf, int order, double tau, 
 
 ts_status finish_sum(ts_ctx *ctx, int nblk, int K, double *out)
 {
+    if (K > kMaxOut)
+        return fail(ctx, TS_ERR_ARG, "reduction larger than the read-back buffer");
     // partial sums live in dpart[0 .. nblk*K); the final sums go after them
     double *dfin = ctx->dpart + (size_t)nblk * K;
     k_sum_final<<<1, 64, 0, ctx->stream>>>(ctx->dpart, nblk, K, dfin);
@@ -986,9 +990,12 @@ ts_status sum_overlap(ts_ctx *ctx, const void *a, const void *b, double *out2)
 
 // <H_a> for a = x (pcq 2: Y^dag = 2^{-N/2} W (-1)^pc) or y (pcq 3: X^dag = 2^{-N/2} D W (-i)^pc):
 // one Walsh-Hadamard layer on a copy, then sum |phi_s|^2 E_a(s) 2^{-N}.
-ts_status rotated_energy(ts_ctx *ctx, int alpha, double *out)
+// Copies the state into the scratch buffer rotated into the eigenbasis of S^x (alpha = 0)
+// or S^y (alpha = 1): one Walsh-Hadamard layer between two diagonal slots, so that
+// |scratch_s|^2 2^-N is the probability of the x or y configuration s (bit 1 = +1/2).
+ts_status frame_copy(ts_ctx *ctx, int alpha)
 {
-    ts_status st = ensure_buf(ctx, ctx->scratch, "energy scratch buffer");
+    ts_status st = ensure_buf(ctx, ctx->scratch, "observable scratch buffer");
     if (st)
         return st;
     TS_CUDA(ctx, cudaMemcpyAsync(ctx->scratch.p, ctx->psi.p, state_bytes(ctx), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -996,7 +1003,46 @@ ts_status rotated_energy(ts_ctx *ctx, int alpha, double *out)
     sl[0].t = 0.0;
     sl[0].pcq = alpha == 0 ? 2 : 3;
     sl[1].t = 0.0;
-    st = run_slots(ctx, ctx->sched_obs, ctx->scratch.p, 0, 0.0, 1, 10 + alpha, sl);
+    return run_slots(ctx, ctx->sched_obs, ctx->scratch.p, 0, 0.0, 1, 10 + alpha, sl);
+}
+
+// Joint bit weights of a state (k_sum_pairs): out[0] = total, out[1 + i] singles,
+// out[1 + N + pair(i, j)] pairs.
+ts_status sum_pairs(ts_ctx *ctx, const void *buf, double *out)
+{
+    const int N = ctx->N;
+    const int K = 1 + N + N * (N - 1) / 2;
+    const unsigned nb = red_blocks(ctx, 256 * 32);
+    ts_status st = ensure_part(ctx, (size_t)nb * K + K);
+    if (st)
+        return st;
+    const size_t smem = (size_t)K * sizeof(double);
+    if (ctx->prec == TS_C64)
+        k_sum_pairs<float2><<<nb, 256, smem, ctx->stream>>>((const float2 *)buf, N, ctx->dpart);
+    else
+        k_sum_pairs<double2><<<nb, 256, smem, ctx->stream>>>((const double2 *)buf, N, ctx->dpart);
+    ctx->launches++;
+    TS_CUDA(ctx, cudaGetLastError());
+    return finish_sum(ctx, (int)nb, K, out);
+}
+
+// <S^a_i S^a_j> = sum_s w(s) (b_i - 1/2)(b_j - 1/2) from the joint bit weights, times wscale.
+void pairs_to_correlations(int N, const double *v, double wscale, double *out)
+{
+    for (int i = 0; i < N; i++) {
+        out[i * N + i] = 0.25 * v[0] * wscale;
+        for (int j = i + 1; j < N; j++) {
+            const double pij = v[1 + N + pair_index(i, j, N)];
+            const double c = (pij - 0.5 * (v[1 + i] + v[1 + j]) + 0.25 * v[0]) * wscale;
+            out[i * N + j] = c;
+            out[j * N + i] = c;
+        }
+    }
+}
+
+ts_status rotated_energy(ts_ctx *ctx, int alpha, double *out)
+{
+    ts_status st = frame_copy(ctx, alpha);
     if (st)
         return st;
     double v = 0.0;
@@ -1086,7 +1132,7 @@ ts_status ts_create(ts_ctx **out, int N, const double *Jx, const double *Jy, con
     if (e == cudaSuccess)
         e = cudaMemcpy(ctx->dhh, ctx->hh.data(), ctx->hh.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMallocHost(&ctx->hout, (kMaxN + 8) * sizeof(double));
+        e = cudaMallocHost(&ctx->hout, kMaxOut * sizeof(double));
     if (e != cudaSuccess) {
         st = (e == cudaErrorMemoryAllocation) ? TS_ERR_OOM : TS_ERR_CUDA;
         ts_destroy(ctx);
@@ -1239,6 +1285,37 @@ ts_status ts_observe(ts_ctx *ctx, int what, double *out)
             out[1] = ov[1];
         }
         return TS_OK;
+    }
+    case TS_SZSZ:
+    case TS_SXSX:
+    case TS_SYSY: {
+        const int alpha = what == TS_SXSX ? 0 : (what == TS_SYSY ? 1 : 2);
+        const void *buf = ctx->psi.p;
+        double wscale = 1.0;
+        if (alpha < 2) {
+            st = frame_copy(ctx, alpha);
+            if (st)
+                return st;
+            buf = ctx->scratch.p;
+            wscale = std::ldexp(1.0, -N);
+        }
+        std::vector<double> v(1 + N + N * (N - 1) / 2);
+        st = sum_pairs(ctx, buf, v.data());
+        if (!st)
+            pairs_to_correlations(N, v.data(), wscale, out);
+        return st;
+    }
+    case TS_SX:
+    case TS_SY: {
+        st = frame_copy(ctx, what == TS_SX ? 0 : 1);
+        if (st)
+            return st;
+        std::vector<double> v(N + 1);
+        st = sum_sz(ctx, ctx->scratch.p, v.data());
+        if (!st)
+            for (int i = 0; i < N; i++)
+                out[i] = std::ldexp(v[1 + i] - 0.5 * v[0], -N);
+        return st;
     }
     case TS_ENERGY: {
         double ez = 0.0, ex = 0.0, ey = 0.0;

@@ -259,6 +259,131 @@ __global__ void __launch_bounds__(256) k_sum_sz(const C *__restrict__ psi, int N
         part[(size_t)blockIdx.x * (N + 1) + i] = acc_sh[i];
 }
 
+// Joint bit weights for two-spin correlations.  Per block, FP64, stride K = 1 + N + N(N-1)/2:
+//   [0] = sum_s w(s),  [1 + i] = sum_s w(s) b_i(s),  [1 + N + pair(i, j)] = sum_s w(s) b_i(s) b_j(s)
+// with w(s) = |psi_s|^2, b_i the bits of s and pair(i, j) (i < j) the row-major index of the
+// strict upper triangle.  Each block iteration covers 2^13 consecutive amplitudes: thread bits
+// are global bits 0..7, the 32 per-thread amplitudes global bits 8..12, the higher bits are
+// constant over the range.  The 92 in-range sums (total, 13 singles, 78 pairs) are formed in the
+// amplitudes' precision and added, with the constant high bits, to FP64 totals.
+__host__ __device__ constexpr int pair_index(int i, int j, int N) { return i * N - i * (i + 1) / 2 + (j - i - 1); }
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_sum_pairs(const C *__restrict__ psi, int N, double *__restrict__ part)
+{
+    using A = typename AccOf<C>::T;
+    constexpr int LB = 5, TBITS = 8, RBITS = LB + TBITS;
+    constexpr int NV = 1 + RBITS + RBITS * (RBITS - 1) / 2;   // 92
+    const int K = 1 + N + N * (N - 1) / 2;
+    const uint64_t dim = UINT64_C(1) << N;
+    extern __shared__ double acc_sh[];                       // K doubles
+    __shared__ A bs[NV];
+    __shared__ A red16[16];
+    for (int i = threadIdx.x; i < K; i += blockDim.x)
+        acc_sh[i] = 0.0;
+    __syncthreads();
+    const uint64_t per_block = (uint64_t)blockDim.x << LB;
+    const int nin = N < RBITS ? N : RBITS;                   // bits inside one range
+    for (uint64_t base = (uint64_t)blockIdx.x * per_block; base < dim; base += (uint64_t)gridDim.x * per_block) {
+        // per-thread sums over its 32 amplitudes: total, per register bit, per register-bit pair
+        A q[32];
+        const uint64_t s0 = base + threadIdx.x;
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+            C a;
+            a.x = 0;
+            a.y = 0;
+            const uint64_t s = s0 + ((uint64_t)j << TBITS);
+            if (s < dim)
+                a = psi[s];
+            q[j] = (A)a.x * (A)a.x + (A)a.y * (A)a.y;
+        }
+        A tot = A(0), low[LB], low2[LB * (LB - 1) / 2];
+#pragma unroll
+        for (int b = 0; b < LB; b++)
+            low[b] = A(0);
+#pragma unroll
+        for (int k = 0; k < LB * (LB - 1) / 2; k++)
+            low2[k] = A(0);
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+            tot += q[j];
+#pragma unroll
+            for (int b = 0; b < LB; b++)
+                if ((j >> b) & 1)
+                    low[b] += q[j];
+            int k = 0;
+#pragma unroll
+            for (int b1 = 0; b1 < LB; b1++)
+#pragma unroll
+                for (int b2 = b1 + 1; b2 < LB; b2++, k++)
+                    if (((j >> b1) & 1) && ((j >> b2) & 1))
+                        low2[k] += q[j];
+        }
+        // the block's 92 sums, 16 at a time (register pressure); local bit l is thread bit l
+        // (l < 8) or register bit l - 8
+        const uint32_t t = threadIdx.x;
+        auto value = [&](int k) -> A {
+            if (k == 0)
+                return tot;
+            if (k <= RBITS) {
+                const int l = k - 1;
+                return l < TBITS ? (((t >> l) & 1) ? tot : A(0)) : low[l - TBITS];
+            }
+            int r = k - 1 - RBITS, l1 = 0;
+            while (r >= RBITS - 1 - l1) {
+                r -= RBITS - 1 - l1;
+                l1++;
+            }
+            const int l2 = l1 + 1 + r;
+            if (l2 < TBITS)
+                return (((t >> l1) & 1) && ((t >> l2) & 1)) ? tot : A(0);
+            if (l1 < TBITS)
+                return ((t >> l1) & 1) ? low[l2 - TBITS] : A(0);
+            return low2[pair_index(l1 - TBITS, l2 - TBITS, LB)];
+        };
+#pragma unroll
+        for (int r0 = 0; r0 < NV; r0 += 16) {
+            A v[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++)
+                v[i] = (r0 + i < NV) ? value(r0 + i) : A(0);
+            block_sum<16>(v, red16);
+            if (threadIdx.x < 16 && r0 + (int)threadIdx.x < NV)
+                bs[r0 + threadIdx.x] = red16[threadIdx.x];
+        }
+        __syncthreads();
+        // add to the FP64 totals; the bits above the range are those of base
+        for (int e = threadIdx.x; e < K; e += blockDim.x) {
+            double add;
+            if (e == 0) {
+                add = (double)bs[0];
+            } else if (e <= N) {
+                const int i = e - 1;
+                add = i < nin ? (double)bs[1 + i] : (((base >> i) & 1) ? (double)bs[0] : 0.0);
+            } else {
+                // invert the pair index
+                int r = e - 1 - N, i = 0;
+                while (r >= N - 1 - i) {
+                    r -= N - 1 - i;
+                    i++;
+                }
+                const int j = i + 1 + r;
+                if (j < nin)
+                    add = (double)bs[1 + RBITS + pair_index(i, j, RBITS)];
+                else if (i < nin)
+                    add = ((base >> j) & 1) ? (double)bs[1 + i] : 0.0;
+                else
+                    add = (((base >> i) & 1) && ((base >> j) & 1)) ? (double)bs[0] : 0.0;
+            }
+            acc_sh[e] += add;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < K; i += blockDim.x)
+        part[(size_t)blockIdx.x * K + i] = acc_sh[i];
+}
+
 // Per block: sum |psi|^2 over a grid-stride range; per thread FP32 (complex64) pairwise
 // sums of 32 amplitudes added to an FP64 running total, one FP64 block reduction.
 template <typename C>

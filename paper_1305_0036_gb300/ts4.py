@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libts4.so")
 TS_OK, TS_ERR_ARG, TS_ERR_OOM, TS_ERR_CUDA, TS_ERR_TIMEOUT, TS_ERR_STATE = 0, -1, -2, -3, -4, -5
 TS_C64, TS_C128 = 0, 1
 TS_NORM, TS_ENERGY, TS_SZ, TS_ECHO, TS_OVERLAP = 1, 2, 3, 4, 5
+TS_SZSZ, TS_SXSX, TS_SYSY, TS_SX, TS_SY = 6, 7, 8, 9, 10
 TS_KERNEL_FUSED, TS_KERNEL_BASIC = 0, 1
 _STATUS = {0: "TS_OK", -1: "TS_ERR_ARG", -2: "TS_ERR_OOM", -3: "TS_ERR_CUDA", -4: "TS_ERR_TIMEOUT",
            -5: "TS_ERR_STATE"}
@@ -363,6 +364,20 @@ class Context:
 
     def sz(self):
         return ts_observe(self.ctx, TS_SZ, self.N)
+
+    def magnetization(self, axis="z"):
+        """<S^axis_j> for j = 1..N (axis x or y uses a rotated scratch copy)."""
+        if axis == "z":
+            return self.sz()
+        self._aux("scratch")
+        return ts_observe(self.ctx, {"x": TS_SX, "y": TS_SY}[axis], self.N)
+
+    def correlations(self, axis="z"):
+        """<S^axis_i S^axis_j> as an N x N array (axis x or y uses a rotated scratch copy)."""
+        if axis != "z":
+            self._aux("scratch")
+        what = {"z": TS_SZSZ, "x": TS_SXSX, "y": TS_SYSY}[axis]
+        return ts_observe(self.ctx, what, self.N * self.N).reshape(self.N, self.N)
 
     def echo(self):
         return float(ts_observe(self.ctx, TS_ECHO, 1)[0])

@@ -27,3 +27,12 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="module")
+def ts4():
+    """The CUDA library's binding, built in-tree first (GPU tests only)."""
+    from paper_1305_0036_gb300 import build
+    build.build()
+    from paper_1305_0036_gb300 import ts4 as m
+    return m

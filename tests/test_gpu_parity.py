@@ -19,12 +19,6 @@ pytestmark = pytest.mark.gpu
 U32 = 2.0 ** -24
 
 
-@pytest.fixture(scope="module")
-def ts4():
-    from paper_1305_0036_gb300 import build
-    build.build()
-    from paper_1305_0036_gb300 import ts4 as m
-    return m
 
 
 def _ham(s):
