@@ -83,6 +83,9 @@ struct Schedule {
     size_t tab_size = 0;
     void *dtab = nullptr;                // device copy, owned by this schedule
     size_t dtab_cap = 0;
+    std::vector<uint4> iomap;            // per group, per thread: I/O-layout offset and base (host image)
+    void *dmap = nullptr;                // device copy
+    size_t dmap_cap = 0;                 // bytes
     double *dtheta = nullptr;            // frame angles of every (slot, group), owned by this schedule
     void *dgfield = nullptr;             // fields g_l per frame (TB values of the kernel's precision), same allocation
     size_t dtheta_cap = 0;               // bytes of the allocation
@@ -91,8 +94,12 @@ struct Schedule {
 // Frees S's device tables once the stream's queued passes (which read them) are done.
 void release_tables(Schedule &S, cudaStream_t st)
 {
-    if (S.dtab || S.dtheta)
+    if (S.dtab || S.dtheta || S.dmap)
         cudaStreamSynchronize(st);
+    if (S.dmap)
+        cudaFree(S.dmap);
+    S.dmap = nullptr;
+    S.dmap_cap = 0;
     if (S.dtab)
         cudaFree(S.dtab);
     if (S.dtheta)
@@ -721,6 +728,23 @@ ts_status prepare_fused(ts_ctx *ctx, Schedule &S)
     S.io.clear();
     for (size_t gi = 0; gi < S.groups.size(); gi++)
         S.io.push_back(make_io(S.groups[gi], TB, RB, ES, io_chunk(S.groups[gi])));
+    // per group and thread of the I/O layout: global offset of its base and its local base
+    const int NT = 1 << (TB - RB);
+    S.iomap.assign(S.groups.size() * (size_t)NT, make_uint4(0, 0, 0, 0));
+    for (size_t gi = 0; gi < S.groups.size(); gi++) {
+        const Group &g = S.groups[gi];
+        auto gpos = [&](int l) { return l < g.h ? g.w + l : l - g.h; };
+        for (int tid = 0; tid < NT; tid++) {
+            uint32_t base = 0;
+            uint64_t off = 0;
+            for (int t = 0; t < TB - RB; t++)
+                if ((tid >> t) & 1) {
+                    base |= 1u << S.io[gi].bits[t];
+                    off |= UINT64_C(1) << gpos(S.io[gi].bits[t]);
+                }
+            S.iomap[gi * NT + tid] = make_uint4((uint32_t)off, (uint32_t)(off >> 32), base, 0);
+        }
+    }
     const int64_t L = (int64_t)S.slots.size() - 1;
     S.passes = make_passes(S.groups, L, TB, RB);
     S.tab_size = tab_size(ctx->prec, TB);
@@ -787,6 +811,18 @@ ts_status prepare_fused(ts_ctx *ctx, Schedule &S)
     S.dgfield = S.dtheta ? static_cast<void *>(S.dtheta + ntheta) : nullptr;
     if (!S.tabs.empty())
         TS_CUDA(ctx, cudaMemcpyAsync(S.dtab, S.tabs.data(), S.tabs.size(), cudaMemcpyHostToDevice, ctx->stream));
+    const size_t map_bytes = S.iomap.size() * sizeof(uint4);
+    if (map_bytes > S.dmap_cap) {
+        if (S.dmap) {
+            TS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            cudaFree(S.dmap);
+            S.dmap = nullptr;
+            S.dmap_cap = 0;
+        }
+        TS_CUDA(ctx, cudaMalloc(&S.dmap, map_bytes));
+        S.dmap_cap = map_bytes;
+    }
+    TS_CUDA(ctx, cudaMemcpyAsync(S.dmap, S.iomap.data(), map_bytes, cudaMemcpyHostToDevice, ctx->stream));
     for (const auto &j : jobs) {
         const Group &g = S.groups[j.group];
         const int N = ctx->N;
@@ -818,6 +854,19 @@ const void *gfield_at(const ts_ctx *ctx, const Schedule &S, size_t off)
     return static_cast<const double *>(S.dgfield) + off * ctx->TB;
 }
 
+// The I/O layout of group gi: the per-thread table and the register bits' global offsets.
+void set_io_args(TileArgs &a, const ts_ctx *ctx, const Schedule &S, int gi)
+{
+    const int TB = ctx->TB, RB = ctx->RB, NT = 1 << (TB - RB);
+    const Group &g = S.groups[gi];
+    a.iomap = static_cast<const uint4 *>(S.dmap) + (size_t)gi * NT;
+    const int W = S.io[gi].chunk == 0 ? 0 : (RB < TB - RB ? RB : TB - RB);
+    for (int b = 0; b < RB; b++) {
+        const int l = W + b;
+        a.gst[b] = UINT64_C(1) << (l < g.h ? g.w + l : l - g.h);
+    }
+}
+
 ts_status run_fused(ts_ctx *ctx, void *buf, const Schedule &S)
 {
     const HamDev hd = ham_dev(ctx);
@@ -839,6 +888,7 @@ ts_status run_fused(ts_ctx *ctx, void *buf, const Schedule &S)
         a.ham = hd;
         a.theta = p.slot >= 0 ? S.dtheta + p.theta_off : nullptr;
         a.gfield = p.slot >= 0 ? gfield_at(ctx, S, p.theta_off) : nullptr;
+        set_io_args(a, ctx, S, p.group);
         const uint64_t nblk = UINT64_C(1) << (ctx->N - (g.c + g.h));
         cudaError_t e = launch_tile(ctx, ctx->TB, buf, a, S.dtab, nblk);
         ctx->launches++;
@@ -871,11 +921,15 @@ ts_status run_slots(ts_ctx *ctx, Schedule &S, void *buf, int order, double tau, 
             const size_t keep_cap = S.dtab_cap;
             double *keep_th = S.dtheta;
             const size_t keep_th_cap = S.dtheta_cap;  // (dgfield is re-derived by prepare_fused)
+            void *keep_map = S.dmap;
+            const size_t keep_map_cap = S.dmap_cap;
             S = Schedule();
             S.dtab = keep;
             S.dtab_cap = keep_cap;
             S.dtheta = keep_th;
             S.dtheta_cap = keep_th_cap;
+            S.dmap = keep_map;
+            S.dmap_cap = keep_map_cap;
             S.slots = slots;
             st = prepare_fused(ctx, S);
             if (st == TS_OK) {
@@ -1602,6 +1656,7 @@ ts_status batch_prepare(ts_batch *b, double tau, int64_t n)
             a.ham = ham_dev(c);
             a.theta = hp.slot >= 0 ? S.dtheta + hp.theta_off : nullptr;
             a.gfield = hp.slot >= 0 ? gfield_at(c, S, hp.theta_off) : nullptr;
+            set_io_args(a, c, S, hp.group);
             start += (uint32_t)((uint64_t)b->nstates[s] << bs.tile_shift);
         }
         b->blocks[p] = start;

@@ -91,6 +91,8 @@ struct TileArgs {
     HamDev ham;
     const double *theta; // per frame f: (t E_FF(f) + th0) / pi reduced to [-1, 1]  (k_frame_terms)
     const void *gfield;  // per frame f: g_l(f) for the TB tile spins, R precision  (k_frame_terms)
+    const uint4 *iomap;  // per thread of the I/O layout: (global offset lo, hi, local base, 0)
+    uint64_t gst[8];     // global offset of each register bit of the I/O layout
 };
 
 // The frame-dependent parts of a slot's angle, for every tile f of a geometry
@@ -556,9 +558,8 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
 {
     using K = TileKernel<R, TB, RB>;
     using C = typename CT<R>::T;
-    constexpr int NR = K::NR, NTB = K::NTB, ES = K::ES;
+    constexpr int NR = K::NR, ES = K::ES;
     const int kio = a.io.chunk;
-    const int Wio = kio == 0 ? 0 : chunk_w<TB, RB>(1);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
     __shared__ TileShared<R, TB, RB> sh;
@@ -590,21 +591,15 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
             qv = tb->QK[tid];
     }
 
-    // ---- I/O layout: this thread's local base and its global offsets
-    uint32_t base_io = 0;
-#pragma unroll
-    for (int t = 0; t < NTB; t++)
-        base_io |= ((tid >> t) & 1u) << a.io.bits[t];
-    auto gpos = [&](int l) { return l < h ? w + l : l - h; };
-    uint64_t gthr = gbase;
-#pragma unroll
-    for (int t = 0; t < NTB; t++)
-        if ((tid >> t) & 1u)
-            gthr |= UINT64_C(1) << gpos(a.io.bits[t]);
+    // ---- I/O layout: this thread's local base and global offset (host table) and the
+    // global offsets of the register bits
+    const uint4 iom = a.iomap[tid];
+    const uint32_t base_io = iom.z;
+    uint64_t gthr = gbase | ((uint64_t)iom.y << 32 | iom.x);
     uint64_t gst[RB];
 #pragma unroll
     for (int b = 0; b < RB; b++)
-        gst[b] = UINT64_C(1) << gpos(Wio + b);
+        gst[b] = a.gst[b];
 
     const uint32_t b0 = kio == 0 ? base_io : K::template chunk_base<0>(tid);
     const uint32_t b1 = kio == 1 ? base_io : K::template chunk_base<1>(tid);
