@@ -185,17 +185,26 @@ bool tile_supported(ts_prec p, int tb)
 int default_tile(ts_prec) { return 12; }  // fastest at N=28 on GB300 for both precisions (measured)
 int default_cbits(ts_prec p) { return p == TS_C64 ? 3 : 2; }
 
-template <typename R, int TB, int RB>
-cudaError_t launch_tile_t(cudaStream_t st, void *psi, const TileArgs &a, const void *tabs, uint64_t nblk)
+template <typename R, int TB, int RB, bool SLOT>
+cudaError_t launch_tile_s(cudaStream_t st, void *psi, const TileArgs &a, const void *tabs, uint64_t nblk)
 {
     using K = TileKernel<R, TB, RB>;
     constexpr size_t smem = sizeof(typename CT<R>::T) * K::SMEM_ELEMS;
-    cudaError_t e = cudaFuncSetAttribute(k_tile<R, TB, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_tile<R, TB, RB, SLOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess)
         return e;
-    k_tile<R, TB, RB><<<(unsigned)nblk, K::NT, smem, st>>>((typename CT<R>::T *)psi, a,
-                                                            (const TileTab<R, TB, RB> *)tabs);
+    k_tile<R, TB, RB, SLOT><<<(unsigned)nblk, K::NT, smem, st>>>((typename CT<R>::T *)psi, a,
+                                                                  (const TileTab<R, TB, RB> *)tabs);
     return cudaGetLastError();
+}
+
+// Passes without a slot run the kernel compiled without the slot machinery.
+template <typename R, int TB, int RB>
+cudaError_t launch_tile_t(cudaStream_t st, void *psi, const TileArgs &a, const void *tabs, uint64_t nblk)
+{
+    return a.has_slot ? launch_tile_s<R, TB, RB, true>(st, psi, a, tabs, nblk)
+                      : launch_tile_s<R, TB, RB, false>(st, psi, a, tabs, nblk);
 }
 
 cudaError_t launch_tile(const ts_ctx *ctx, int TB, void *psi, const TileArgs &a, const void *tabs, uint64_t nblk)

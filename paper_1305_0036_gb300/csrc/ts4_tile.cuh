@@ -552,7 +552,9 @@ template <typename R, int TB, int RB> struct TileKernel {
 };
 
 // One tile f of the state psi through the pass described by a.
-template <typename R, int TB, int RB>
+// SLOT = false compiles a pass without a slot (the middle passes): no slot tables, no
+// per-thread factors in shared memory, fewer registers, so more blocks per SM.
+template <typename R, int TB, int RB, bool SLOT>
 __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, const TileArgs &a,
                                           const TileTab<R, TB, RB> *__restrict__ tabs, uint64_t f)
 {
@@ -562,7 +564,8 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
     const int kio = a.io.chunk;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
-    __shared__ TileShared<R, TB, RB> sh;
+    __shared__ typename std::conditional<SLOT, TileShared<R, TB, RB>, char>::type sh_store;
+    auto &sh = sh_store;
 
     const uint32_t tid = threadIdx.x;
     const int c = a.c, w = a.w, h = a.h;
@@ -577,18 +580,20 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
 #pragma unroll
     for (int b = 0; b < RB; b++)
         tc[b] = R(0);
-    if (a.has_slot) {
-        const TileTab<R, TB, RB> *tb = tabs + a.tab;
-        if (tid < TB)
-            gv = static_cast<const R *>(a.gfield)[f * TB + tid];
-        if (tid == 32)
-            thv = a.theta[f];
-        tp = tb->TP[tid];
+    if constexpr (SLOT) {
+        if (a.has_slot) {
+            const TileTab<R, TB, RB> *tb = tabs + a.tab;
+            if (tid < TB)
+                gv = static_cast<const R *>(a.gfield)[f * TB + tid];
+            if (tid == 32)
+                thv = a.theta[f];
+            tp = tb->TP[tid];
 #pragma unroll
-        for (int b = 0; b < RB; b++)
-            tc[b] = tb->TC[b][tid];
-        if (tid < NR)
-            qv = tb->QK[tid];
+            for (int b = 0; b < RB; b++)
+                tc[b] = tb->TC[b][tid];
+            if (tid < NR)
+                qv = tb->QK[tid];
+        }
     }
 
     // ---- I/O layout: this thread's local base and global offset (host table) and the
@@ -623,41 +628,45 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
     R scale = R(1);
     float srel = 0.0f;                 // exact scale / rounded scale - 1 (c64: sqrt 1/2 is not exact)
     const int mode = a.exact_sincos;   // c64 per-amplitude factor: 0 tiny |y|, 1 small |y|, 2 any
-    if (a.has_slot) {
-        pcq = a.slot.pcq;
-        if constexpr (sizeof(R) == 4) {
-            scale = a.slot.scale_f;
-            srel = a.slot.srel;
-        } else {
-            scale = a.slot.scale;
+    if constexpr (SLOT) {
+        if (a.has_slot) {
+            pcq = a.slot.pcq;
+            if constexpr (sizeof(R) == 4) {
+                scale = a.slot.scale_f;
+                srel = a.slot.srel;
+            } else {
+                scale = a.slot.scale;
+            }
+            if (tid < TB)
+                sh.g[tid] = gv;
+            if (tid == 32) {
+                sh.th = thv;
+                sh.th_hi = (float)thv;
+                sh.th_lo = (float)(thv - (double)(float)thv);
+                sh.pcF = __popcll(gbase);
+            }
+            if (tid < NR)
+                sh.Q[tid] = qv;
         }
-        if (tid < TB)
-            sh.g[tid] = gv;
-        if (tid == 32) {
-            sh.th = thv;
-            sh.th_hi = (float)thv;
-            sh.th_lo = (float)(thv - (double)(float)thv);
-            sh.pcF = __popcll(gbase);
-        }
-        if (tid < NR)
-            sh.Q[tid] = qv;
     }
     __syncthreads();
 
     // ---- per-thread slot factors, computed before the tile occupies the registers
-    if (a.has_slot) {
-        int kph = 0;
-        for (int s = 0; s < a.nsteps; s++)
-            if (a.steps[s].ph)
-                kph = a.steps[s].k;
-        if constexpr (sizeof(R) == 4) {
-            SlotThreadC64<RB> o;
-            slot_thread_c64<TB, RB>(o, base_of(kph), kph, sh, pcq, (float)scale, srel, tp, tc);
-            sh.th_f.put(tid, o);
-        } else {
-            SlotThreadC128 o;
-            slot_thread_c128<TB, RB>(o, base_of(kph), chunk_w<TB, RB>(kph), sh, pcq, (double)scale, tp, tc);
-            sh.th_f.put(tid, o);
+    if constexpr (SLOT) {
+        if (a.has_slot) {
+            int kph = 0;
+            for (int s = 0; s < a.nsteps; s++)
+                if (a.steps[s].ph)
+                    kph = a.steps[s].k;
+            if constexpr (sizeof(R) == 4) {
+                SlotThreadC64<RB> o;
+                slot_thread_c64<TB, RB>(o, base_of(kph), kph, sh, pcq, (float)scale, srel, tp, tc);
+                sh.th_f.put(tid, o);
+            } else {
+                SlotThreadC128 o;
+                slot_thread_c128<TB, RB>(o, base_of(kph), chunk_w<TB, RB>(kph), sh, pcq, (double)scale, tp, tc);
+                sh.th_f.put(tid, o);
+            }
         }
     }
 
@@ -686,8 +695,10 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
             cur = k;
         }
         wht_regs<RB>(x, d.r0lo, d.r0hi);
-        if (d.ph)
-            K::apply_slot(x, sh, mode);
+        if constexpr (SLOT) {
+            if (d.ph)
+                K::apply_slot(x, sh, mode);
+        }
         wht_regs<RB>(x, d.r1lo, d.r1hi);
     }
     if (cur != kio) {
@@ -734,12 +745,12 @@ __host__ __device__ constexpr int tile_min_blocks(int thread_bits, int reg_elems
     return (65536 / (2 * reg_elems)) >> thread_bits > 0 ? (65536 / (2 * reg_elems)) >> thread_bits : 1;
 }
 
-template <typename R, int TB, int RB>
+template <typename R, int TB, int RB, bool SLOT>
 __global__ void __launch_bounds__(1 << (TB - RB), tile_min_blocks(TB - RB, (int)(sizeof(typename CT<R>::T) / 4) << RB))
 k_tile(typename CT<R>::T *__restrict__ psi, const __grid_constant__ TileArgs a,
        const TileTab<R, TB, RB> *__restrict__ tabs)
 {
-    tile_pass<R, TB, RB>(psi, a, tabs, blockIdx.x);
+    tile_pass<R, TB, RB, SLOT>(psi, a, tabs, blockIdx.x);
 }
 
 // Ensemble pass: every state of every system of a batch through its own pass
@@ -769,7 +780,7 @@ k_tile_batch(const BatchSys *__restrict__ sys, const TileArgs *__restrict__ args
     const uint32_t state = local >> sys[s].tile_shift;
     const uint64_t f = local & ((1u << sys[s].tile_shift) - 1u);
     typename CT<R>::T *psi = reinterpret_cast<typename CT<R>::T *>(sys[s].psi) + ((uint64_t)state << sys[s].n);
-    tile_pass<R, TB, RB>(psi, args[s], reinterpret_cast<const TileTab<R, TB, RB> *>(sys[s].tabs), f);
+    tile_pass<R, TB, RB, true>(psi, args[s], reinterpret_cast<const TileTab<R, TB, RB> *>(sys[s].tabs), f);
 }
 
 } // namespace ts4
