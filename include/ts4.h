@@ -206,6 +206,18 @@ TS4_API double ts_step_bound(const ts_ctx *ctx);
 TS4_API uint64_t ts_tile_global_index(int N, int c, int w, int h, uint64_t f, uint64_t e);
 
 /*
+ * The paper's phase-table mode (Sec. 3.1: the energies of every basis state are
+ * precomputed once and each phase reads them), kept for an A/B comparison with
+ * the bit-test slots.  enable != 0 builds three tables E_x, E_y, E_z of 2^N
+ * floats each (12 bytes per basis state; N = 28: 3 GiB) on the device; the basic
+ * kernel (TS_KERNEL_BASIC) then reads its slot angles from them.  The fused
+ * kernel forms its angles from the bits and ignores the tables.  enable = 0
+ * frees them.  The tables follow later ts_set_transverse_fields calls.
+ * Errors: TS_ERR_OOM if the tables do not fit, TS_ERR_CUDA.
+ */
+TS4_API ts_status ts_set_phase_tables(ts_ctx *ctx, int enable);
+
+/*
  * Autotuner (Sec. 3.4, last paragraph: the best rotation schedule depends on the
  * system size, so the paper searched it by brute force and stored the winners in
  * a file).  Times one TS4 step of length tau, reps times, on a scratch copy of the

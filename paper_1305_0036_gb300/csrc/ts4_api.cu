@@ -135,6 +135,7 @@ struct ts_ctx {
     std::vector<double> Jraw[3];
     std::vector<double> hraw[3];
     double *dJq = nullptr, *dhh = nullptr;
+    float *dE = nullptr;      // phase-table mode: E_x, E_y, E_z per basis state (3 x 2^N floats), or NULL
     Buf psi, ref, scratch;
     bool ref_valid = false;
     double *dpart = nullptr;
@@ -717,10 +718,17 @@ ts_status run_basic(ts_ctx *ctx, void *buf, const std::vector<HostSlot> &slots)
             }
         }
         const Slot sl = slots[k].dev();
-        if (ctx->prec == TS_C64)
+        if (ctx->dE) {
+            const float *E = ctx->dE + (size_t)sl.alpha * dim;
+            if (ctx->prec == TS_C64)
+                k_slot_table<float><<<gs, 256, 0, ctx->stream>>>((float2 *)buf, E, dim, sl);
+            else
+                k_slot_table<double><<<gs, 256, 0, ctx->stream>>>((double2 *)buf, E, dim, sl);
+        } else if (ctx->prec == TS_C64) {
             k_slot_basic<float><<<gs, 256, 0, ctx->stream>>>((float2 *)buf, dim, hd, sl);
-        else
+        } else {
             k_slot_basic<double><<<gs, 256, 0, ctx->stream>>>((double2 *)buf, dim, hd, sl);
+        }
         ctx->launches++;
         TS_CUDA(ctx, cudaGetLastError());
     }
@@ -1223,6 +1231,10 @@ ts_status ts_set_transverse_fields(ts_ctx *ctx, const double *hx, const double *
     TS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     reset_schedule(ctx->sched, ctx->stream);
     reset_schedule(ctx->sched_obs, ctx->stream);
+    if (ctx->dE) {   // the phase tables hold the old fields: rebuild them
+        ts_set_phase_tables(ctx, 0);
+        return ts_set_phase_tables(ctx, 1);
+    }
     return TS_OK;
 }
 
@@ -1427,7 +1439,41 @@ ts_status ts_destroy(ts_ctx *ctx)
     release_tables(ctx->sched_obs, ctx->stream);
     if (ctx->hout)
         cudaFreeHost(ctx->hout);
+    if (ctx->dE)
+        cudaFree(ctx->dE);
     delete ctx;
+    return TS_OK;
+}
+
+ts_status ts_set_phase_tables(ts_ctx *ctx, int enable)
+{
+    if (!ctx)
+        return TS_ERR_ARG;
+    if (!enable) {
+        if (ctx->dE) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->dE);
+        }
+        ctx->dE = nullptr;
+        return TS_OK;
+    }
+    if (ctx->dE)
+        return TS_OK;
+    const uint64_t dim = dim_of(ctx);
+    const size_t bytes = 3 * (size_t)dim * sizeof(float);
+    size_t freeb = 0, totb = 0;
+    TS_CUDA(ctx, cudaMemGetInfo(&freeb, &totb));
+    if (bytes > freeb)
+        return fail(ctx, TS_ERR_OOM, "ts_set_phase_tables: the three 2^N tables do not fit");
+    TS_CUDA(ctx, cudaMalloc(&ctx->dE, bytes));
+    const HamDev hd = ham_dev(ctx);
+    const unsigned gs = grid_for(ctx, dim, 256);
+    for (int a = 0; a < 3; a++) {
+        k_energy_table<<<gs, 256, 0, ctx->stream>>>(ctx->dE + (size_t)a * dim, dim, hd, a);
+        ctx->launches++;
+    }
+    TS_CUDA(ctx, cudaGetLastError());
+    TS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return TS_OK;
 }
 

@@ -77,6 +77,40 @@ __global__ void k_slot_basic(typename CT<R>::T *__restrict__ psi, uint64_t dim, 
     }
 }
 
+// The paper's phase-table mode (Sec. 3.1): E_alpha(s) for every basis state, stored once
+// (FP32, 4 bytes per state and alpha), so that a slot reads its angle instead of forming it
+// from the bits.  Kept for the A/B comparison with the bit-test and the fused kernels.
+static __global__ void k_energy_table(float *__restrict__ E, uint64_t dim, HamDev ham, int alpha)
+{
+    const double *Jq = ham.Jq + (size_t)alpha * ham.N * ham.N;
+    const double *hh = ham.hh + (size_t)alpha * ham.N;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < dim; s += stride)
+        E[s] = (float)energy_bits(s, Jq, hh, ham.N);
+}
+
+// One slot from the energy table: as k_slot_basic, with E_alpha(s) read from E.
+template <typename R>
+__global__ void k_slot_table(typename CT<R>::T *__restrict__ psi, const float *__restrict__ E, uint64_t dim, Slot sl)
+{
+    using C = typename CT<R>::T;
+    const double scale = sl.scale;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < dim; s += stride) {
+        const double th = sl.th0 + sl.t * (double)E[s];
+        double2 f = cexpm_pi(halfturns_2pi(th));
+        f.x *= scale;
+        f.y *= scale;
+        f = cmul_ipow(f, sl.pcq * __popcll(s));
+        const C x = psi[s];
+        const double2 y = cmul(make_double2((double)x.x, (double)x.y), f);
+        C r;
+        r.x = (R)y.x;
+        r.y = (R)y.y;
+        psi[s] = r;
+    }
+}
+
 // ------------------------------------------------------------------ fused tile pass: descriptors
 
 struct StepDesc {

@@ -49,6 +49,7 @@ SIGNATURES = {
     "ts_kernel_launches": (_I64, [_P]),
     "ts_reduce_sz_static": (_I, [_P, _I, _I, _P, _P]),
     "ts_autotune": (_I, [_P, _D, _I, ctypes.c_char_p, _P]),
+    "ts_set_phase_tables": (_I, [_P, _I]),
     "ts_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, _P, _P, _P, _P, _P, _I, _P]),
     "ts_batch_bind_states": (_I, [_P, _I, _P, _SZ]),
     "ts_batch_set_states": (_I, [_P, _I, _P, _I]),
@@ -398,6 +399,10 @@ class Context:
 
     def schedule(self):
         return ts_get_schedule(self.ctx)
+
+    def set_phase_tables(self, enable=True):
+        """The paper's 2^N energy tables for the basic kernel (A/B comparison)."""
+        _check(_lib.ts_set_phase_tables(self.ctx, 1 if enable else 0), self.ctx)
 
     def autotune(self, tau, reps=2, cache_path=None):
         """Brute-force search of the tile shape (library side); returns the best ms per step."""

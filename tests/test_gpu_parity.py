@@ -102,6 +102,33 @@ def test_basic_kernel_matches_oracle(ts4):
     assert np.linalg.norm(got64 - ref) <= _c64_bound(N, 60)
 
 
+def test_phase_table_mode_matches_oracle(ts4):
+    """The paper's 2^N energy tables (Sec. 3.1) behind the basic kernel: same results as the
+    oracle; the energies are stored in FP32, so the angles carry a relative error of 2^-24
+    and the c128 bound is that times the largest angle, summed over the slots."""
+    N = 12
+    s = W.random_system(N, 17, transverse=True)
+    psi0 = W.haar_state(N, 18)
+    tau, n = 0.05, 3
+    ref = oracle.ts4(psi0, _ham(s), tau, n)
+    emax = 0.25 * sum(np.abs(J).sum() for J in (s.Jx, s.Jy, s.Jz)) + 0.5 * sum(
+        np.abs(h).sum() for h in (s.hx, s.hy, s.hz) if h is not None)
+    for prec in ("c128", "c64"):
+        ctx = ts4.Context.from_system(s, prec=prec)
+        ctx.set_schedule(ts4.TS_KERNEL_BASIC, 0, 0)
+        ctx.set_phase_tables(True)
+        ctx.set_state(psi0)
+        ctx.step(tau, n)
+        got = ctx.get_state().astype(np.complex128)
+        if prec == "c128":
+            assert np.abs(got - ref).max() <= 21 * n * tau * emax * 2.0 ** -23
+        else:
+            assert np.linalg.norm(got - ref) <= _c64_bound(N, 20 * n)
+        # tables follow a change of the transverse fields
+        ctx.set_phase_tables(False)
+        ctx.close()
+
+
 @pytest.mark.parametrize("order", [1, 2])
 @pytest.mark.parametrize("N", [13, 16])
 def test_lower_orders_match_oracle(ts4, order, N):
