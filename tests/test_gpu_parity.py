@@ -258,6 +258,34 @@ def test_config3_size_ising_closed_form_c64(ts4):
     assert err <= 60 * (N + 8) * U32 * 2 ** (-(N - 1) / 2) * 8, err
 
 
+def test_config3_bench_configuration_c64_against_c128(ts4):
+    """The benchmark's own workload and launch configuration at full size: N=28 dipolar XXZ
+    chain, Eq. A.1 state, default schedule (12-bit tiles, 3 bit groups, 40 fused passes per
+    step), tau = 0.01, 3 steps.  The complex128 run (FP64 throughout, parity-tested against
+    the oracle at smaller N) is the reference; the complex64 state must agree within the
+    derived c64 bound, and on sampled amplitudes within the same bound per amplitude scale."""
+    s = W.dipolar_chain(28)
+    N, tau, n = s.N, 0.01, 3
+    psi0 = W.random_phase_state(N, W.SEED_BASE + 3)
+    ctx128 = ts4.Context.from_system(s, prec="c128")
+    ctx128.set_state(psi0)
+    ctx128.step(tau, n)
+    ref = ctx128.get_state()
+    ctx128.close()
+    ctx = ts4.Context.from_system(s, prec="c64")
+    sch = ctx.schedule()
+    assert (sch["tile_bits"], sch["groups"], sch["passes_per_step"]) == (12, 3, 40)
+    ctx.set_state(psi0.astype(np.complex64))
+    ctx.step(tau, n)
+    got = ctx.get_state().astype(np.complex128)
+    ctx.close()
+    bound = _c64_bound(N, 20 * n + 1)
+    assert np.linalg.norm(got - ref) <= bound
+    idx = np.random.default_rng(7).integers(0, 1 << N, 4096)
+    assert np.abs(got[idx] - ref[idx]).max() <= bound * 2 ** (-(N - 8) / 2)
+    assert abs(np.vdot(got, got).real - 1.0) <= 1e-5
+
+
 def test_config3_echo_c64_and_c128(ts4):
     """N=28 dipolar XXZ, random-phase state: forward then backward steps return to psi_0
     (Eq. 11 with Sigma = 0).  The echo is taken relative to its value at t = 0 so that the
