@@ -624,13 +624,22 @@ std::vector<HostPass> make_passes(const std::vector<Group> &G, int64_t L, int TB
         P.push_back(make_pass(0, G[0], P_PHASE, (int)L, TB, RB));
         return P;
     }
+    // Visiting order of the groups: the two ends of the zigzag carry the slots and rotate
+    // their group twice, so the largest group (group 0, TB bits) goes between them when
+    // there are three or more groups: its single rotation per layer then runs in a pass
+    // without a slot, and the double rotations fall on the smaller window groups.
+    std::vector<int> perm(g);
+    for (int k = 0; k < g; k++)
+        perm[k] = k;
+    if (g >= 3)
+        std::swap(perm[0], perm[1]);
     P.reserve((size_t)(1 + L * (g - 1)));
-    P.push_back(make_pass(0, G[0], P_PHASE_ROT, 0, TB, RB));
+    P.push_back(make_pass(perm[0], G[perm[0]], P_PHASE_ROT, 0, TB, RB));
     for (int64_t l = 1; l <= L; l++) {
         // layer l visits the groups forward when l is odd, backward when even
         std::vector<int> ord(g);
         for (int k = 0; k < g; k++)
-            ord[k] = (l & 1) ? k : g - 1 - k;
+            ord[k] = perm[(l & 1) ? k : g - 1 - k];
         for (int k = 1; k < g - 1; k++)
             P.push_back(make_pass(ord[k], G[ord[k]], P_ROT, -1, TB, RB));
         const int last = ord[g - 1];

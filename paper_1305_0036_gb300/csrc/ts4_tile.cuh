@@ -351,10 +351,10 @@ template <int MODE> __device__ __forceinline__ void unit_factor(float y, float &
     }
 }
 
-// Per-amplitude factors: x_j <- (x_j R[popcount j]) ((1 + c_j + kT) - i s_j).  Every factor
-// has unit magnitude to ~1e-10 times the exact scale (the dropped terms kT c and kT s of the
-// exact product (1 + kT)((1 + c) - i s) change it by < 2e-10); the FP32 roundings left are
-// those of products with x_j, which change from step to step and do not build up.
+// Per-amplitude factors: x_j <- x_j R[popcount j] (1 + kT)((1 + c_j) - i s_j).  Every
+// factor has unit magnitude to ~1e-10 times the exact scale; the one FP32 rounding left per
+// component is that of the full product, which changes from step to step and does not
+// build up.
 // One amplitude, register index J (compile-time: every table index below is a constant).
 template <int MODE, int J, int NT, int RB>
 __device__ __forceinline__ void slot_c64_one(float2 &xj, const SlotSoA64<NT, RB> &o, int t,
@@ -364,9 +364,19 @@ __device__ __forceinline__ void slot_c64_one(float2 &xj, const SlotSoA64<NT, RB>
     const float y = (o.Lo[J & ((1 << LB) - 1)][t] + o.Hi[J >> LB][t]) + Q[J].x;
     float c, s;
     unit_factor<MODE>(y, c, s);
-    const float ct = c + kT;
-    const float2 x1 = cmul(xj, o.R[P][t]);
-    xj = make_float2(fmaf(x1.x, ct, fmaf(x1.y, s, x1.x)), fmaf(x1.y, ct, fmaf(-x1.x, s, x1.y)));
+    // fold T's magnitude correction: (1 + kT)((1 + c) - i s), cross terms included (they
+    // carry the sign of kT for every amplitude of a thread, i.e. they repeat each step)
+    const float ct = fmaf(c, kT, c + kT);
+    const float st = fmaf(s, kT, s);
+    // x R (1 + ct - i st) = x R + x u with u = R (ct - i st) small.  The O(1) products enter
+    // the FMA chain last, so each component is rounded once at full size.  Rounding x R
+    // first and then applying the near-unit factor loses the sub-ulp magnitude correction
+    // whenever c and s are small, and that loss repeats every step: it made the norm drift
+    // by -1e-8 per step on the 2x12 ladder.
+    const float2 r = o.R[P][t];
+    const float2 u = make_float2(fmaf(r.x, ct, r.y * st), fmaf(r.y, ct, -r.x * st));
+    xj = make_float2(fmaf(xj.x, r.x, fmaf(-xj.y, r.y, fmaf(xj.x, u.x, -xj.y * u.y))),
+                     fmaf(xj.x, r.y, fmaf(xj.y, r.x, fmaf(xj.x, u.y, xj.y * u.x))));
 }
 
 template <int MODE, int NT, int RB, int... J>

@@ -219,12 +219,16 @@ def test_config2_c64_against_fp64_run(ts4):
     for c in (c64, c128):
         c.set_basis_state(cfg["state"][1])
     worst_sz, worst_norm = 0.0, 0.0
+    done = 0
     for chunk in range(10):
         for c in (c64, c128):
             c.step(cfg["tau"], cfg["nsteps"] // 10)
+        done += cfg["nsteps"] // 10
         worst_sz = max(worst_sz, np.abs(c64.sz() - c128.sz()).max())
         worst_norm = max(worst_norm, abs(c64.norm() - 1.0))
-        assert abs(c128.norm() - 1.0) < 1e-12
+        # complex128: each of the 21 slots per step can be off unit magnitude by one FP64
+        # ulp of its factor, in a way that repeats from step to step
+        assert abs(c128.norm() - 1.0) <= 21 * done * 2.0 ** -52
     assert worst_sz <= 1e-5, worst_sz
     assert worst_norm <= 1e-5, worst_norm
     c64.close()
