@@ -140,7 +140,7 @@ template <typename R, int TB, int RB> using TileTab = PassTab<R, TB, RB>;
 // into its low RB - 2 bits (Lo) and its top 2 bits (Hi).
 template <int RB> struct SlotThreadC64 {
     static constexpr int LB = RB - 2;
-    float2 R[RB + 1];  // T i^{pcq p}, p = popcount of the register index
+    float2 R[4];  // T i^{pcq p}, p = popcount of the register index mod 4 (i^4 = 1)
     float Lo[1 << LB];
     float Hi[4];
     float kT;          // |T (1 + kT)| = |scale| to ~1e-14: the FP32 magnitude error of T, removed
@@ -157,7 +157,7 @@ struct SlotThreadC128 {
 // 128 bytes) would put several lanes of a warp on the same bank.
 template <int NT, int RB> struct SlotSoA64 {
     static constexpr int LB = RB - 2;
-    float2 R[RB + 1][NT];
+    float2 R[4][NT];
     float Lo[1 << LB][NT];
     float Hi[4][NT];
     float kT[NT];
@@ -165,7 +165,7 @@ template <int NT, int RB> struct SlotSoA64 {
     __device__ __forceinline__ void put(int t, const SlotThreadC64<RB> &o)
     {
 #pragma unroll
-        for (int k = 0; k <= RB; k++)
+        for (int k = 0; k < 4; k++)
             R[k][t] = o.R[k];
 #pragma unroll
         for (int k = 0; k < (1 << LB); k++)
@@ -282,9 +282,10 @@ __device__ __forceinline__ void slot_thread_c64_w(SlotThreadC64<RB> &o, uint32_t
         const float d = ((p1 - 1.0f) + p2) + (e1 + e2);
         o.kT = fmaf(-0.5f, d, srel);
     }
-    // the factor of register j is T i^{pcq popcount(j)} e^{-i y_j}: keep T i^{pcq p}, p = 0..5
+    // the factor of register j is T i^{pcq popcount(j)} e^{-i y_j}: keep T i^{pcq p} for
+    // p = 0..3 (the power of i repeats with period 4 in the popcount)
 #pragma unroll
-    for (int p = 0; p <= RB; p++)
+    for (int p = 0; p < 4; p++)
         o.R[p] = cmul_ipow(T, (pcq * p) & 3);
     constexpr int LB = RB - 2;
     o.Lo[0] = 0.0f;
@@ -373,7 +374,7 @@ __device__ __forceinline__ void slot_c64_one(float2 &xj, const SlotSoA64<NT, RB>
     // first and then applying the near-unit factor loses the sub-ulp magnitude correction
     // whenever c and s are small, and that loss repeats every step: it made the norm drift
     // by -1e-8 per step on the 2x12 ladder.
-    const float2 r = o.R[P][t];
+    const float2 r = o.R[P & 3][t];
     const float2 u = make_float2(fmaf(r.x, ct, r.y * st), fmaf(r.y, ct, -r.x * st));
     xj = make_float2(fmaf(xj.x, r.x, fmaf(-xj.y, r.y, fmaf(xj.x, u.x, -xj.y * u.y))),
                      fmaf(xj.x, r.y, fmaf(xj.y, r.x, fmaf(xj.x, u.y, xj.y * u.x))));
