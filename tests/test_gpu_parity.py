@@ -80,6 +80,23 @@ def test_fused_c64_matches_oracle(ts4, N, tb64, tb128, cb):
     assert err <= _c64_bound(N, 20 * nsteps), err
 
 
+def test_hundred_steps_multi_group_matches_oracle(ts4):
+    """100 TS4 steps through the fused passes with several bit groups: complex128 on three
+    groups (11-bit tiles, 6 coalescing spins, windows of 3 and 3 spins) within 1e-12 of the
+    oracle, complex64 on two groups within its bound."""
+    N = 17
+    s = W.random_system(N, 117, transverse=True)
+    psi0 = W.haar_state(N, 217)
+    nsteps, tau = 100, 0.03
+    ref = oracle.ts4(psi0, _ham(s), tau, nsteps)
+    got, sched = _gpu_run(ts4, s, psi0, tau, nsteps, "c128", tile=11, cbits=6)
+    assert sched["groups"] == 3
+    assert np.abs(got - ref).max() <= 1e-12
+    got64, sched64 = _gpu_run(ts4, s, psi0, tau, nsteps, "c64", tile=12, cbits=7)
+    assert sched64["groups"] == 2
+    assert np.linalg.norm(got64 - ref) <= _c64_bound(N, 20 * nsteps)
+
+
 def test_c64_large_angles_take_the_exact_path(ts4):
     """A large step (|y| beyond the polynomial's range) must still match the oracle."""
     N = 14
