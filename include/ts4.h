@@ -284,6 +284,25 @@ TS4_API ts_status ts_batch_get_states(ts_batch *b, int sys, void *amps, int on_d
 /* Tile bits and coalescing bits for every system (0 = default); the tile may not exceed the smallest N. */
 TS4_API ts_status ts_batch_set_schedule(ts_batch *b, int tile_bits, int coalesce_bits);
 
+/* The ensemble's tile bits and coalescing bits (either pointer may be NULL). */
+TS4_API ts_status ts_batch_get_schedule(const ts_batch *b, int *tile_bits, int *coalesce_bits);
+
+/*
+ * Autotuner for the ensemble (Sec. 3.4's brute-force schedule search, applied to
+ * the whole batch): times reps ts_batch_step(tau, 1) graph launches for every tile
+ * size this build provides up to the smallest N and every coalescing width 1..4,
+ * and keeps the fastest.  The trials run on the ensemble's own buffers after a
+ * device copy of every state has been taken; the states are copied back at the
+ * end, so they are unchanged.  cache_path (may be NULL): the same file format as
+ * ts_autotune, with the N field set to -(a 31-bit FNV-1a hash of the (N, nstates)
+ * list of the systems); a matching line is used instead of searching (best_ms is
+ * then -1) and a new result is appended.  best_ms (may be NULL) receives the best
+ * time per ensemble step in ms.
+ * Errors: TS_ERR_ARG, TS_ERR_STATE (a system has no states), TS_ERR_OOM (no room
+ * for the copy of the states), TS_ERR_CUDA.
+ */
+TS4_API ts_status ts_batch_autotune(ts_batch *b, double tau, int reps, const char *cache_path, double *best_ms);
+
 /* nsteps TS4 steps of length tau for every state: one CUDA graph launch (Sec. 2). */
 TS4_API ts_status ts_batch_step(ts_batch *b, double tau, int64_t nsteps);
 

@@ -2087,4 +2087,122 @@ ts_status ts_autotune(ts_ctx *ctx, double tau, int reps, const char *cache_path,
     return ts_set_schedule(ctx, TS_KERNEL_FUSED, btb, bcb);
 }
 
+ts_status ts_batch_get_schedule(const ts_batch *b, int *tile_bits, int *coalesce_bits)
+{
+    if (!b)
+        return TS_ERR_ARG;
+    if (tile_bits)
+        *tile_bits = b->TB;
+    if (coalesce_bits)
+        *coalesce_bits = b->cbits;
+    return TS_OK;
+}
+
+ts_status ts_batch_autotune(ts_batch *b, double tau, int reps, const char *cache_path, double *best_ms)
+{
+    if (!b)
+        return TS_ERR_ARG;
+    if (!std::isfinite(tau) || reps < 1)
+        return bfail(b, TS_ERR_ARG, "ts_batch_autotune: tau must be finite and reps >= 1");
+    for (int s = 0; s < b->nsys; s++)
+        if (!b->psi[s].p)
+            return bfail(b, TS_ERR_STATE, "ts_batch_autotune: a system has no states set");
+    // cache key: -(FNV-1a of the (N, nstates) list), so that it never equals a system size
+    uint32_t h = 2166136261u;
+    auto mix = [&h](uint32_t v) {
+        for (int k = 0; k < 4; k++) {
+            h ^= (v >> (8 * k)) & 0xffu;
+            h *= 16777619u;
+        }
+    };
+    int nmin = 64;
+    std::vector<size_t> bytes(b->nsys);
+    size_t total = 0;
+    for (int s = 0; s < b->nsys; s++) {
+        mix((uint32_t)b->sys[s]->N);
+        mix((uint32_t)b->nstates[s]);
+        nmin = std::min(nmin, b->sys[s]->N);
+        bytes[s] = state_bytes(b->sys[s]) * (size_t)b->nstates[s];
+        total += bytes[s];
+    }
+    const int key = -(int)(h & 0x7fffffffu);
+    const std::string gpu = device_name();
+    int tb = 0, cb = 0;
+    if (tune_lookup(cache_path, gpu, key, (int)b->prec, &tb, &cb) && tile_supported(b->prec, tb) && tb <= nmin) {
+        if (best_ms)
+            *best_ms = -1.0;
+        return ts_batch_set_schedule(b, tb, cb);
+    }
+    // the trials run on the ensemble's buffers: keep a device copy of every state
+    void *save = nullptr;
+    cudaError_t ce = cudaMalloc(&save, total);
+    if (ce != cudaSuccess)
+        return bfail(b, ce == cudaErrorMemoryAllocation ? TS_ERR_OOM : TS_ERR_CUDA,
+                     "ts_batch_autotune: no room for a copy of the states");
+    size_t off = 0;
+    for (int s = 0; s < b->nsys && ce == cudaSuccess; s++) {
+        ce = cudaMemcpyAsync((char *)save + off, b->psi[s].p, bytes[s], cudaMemcpyDeviceToDevice, b->stream);
+        off += bytes[s];
+    }
+    const int keep_tb = b->TB, keep_cb = b->cbits;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ce == cudaSuccess)
+        ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess)
+        ce = cudaEventCreate(&e1);
+    ts_status st = ce == cudaSuccess ? TS_OK : TS_ERR_CUDA;
+    double best = 1e300;
+    int btb = keep_tb, bcb = keep_cb;
+    const int tbs64[3] = {12, 13, 14}, tbs128[3] = {11, 12, 13};
+    for (int i = 0; i < 3 && !st; i++) {
+        const int t = b->prec == TS_C64 ? tbs64[i] : tbs128[i];
+        if (t > nmin)
+            continue;
+        for (int c = 1; c <= 4 && !st; c++) {
+            if (c > t - reg_bits(b->prec))
+                continue;
+            st = ts_batch_set_schedule(b, t, c);
+            if (!st)
+                st = ts_batch_step(b, tau, 1);   // graph capture and warm-up
+            if (!st && cudaEventRecord(e0, b->stream) != cudaSuccess)
+                st = TS_ERR_CUDA;
+            for (int r = 0; r < reps && !st; r++)
+                st = ts_batch_step(b, tau, 1);
+            if (!st && (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+                st = TS_ERR_CUDA;
+            float ms = 0.f;
+            if (!st && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms / reps < best) {
+                best = ms / reps;
+                btb = t;
+                bcb = c;
+            }
+        }
+    }
+    const std::string trial_err = b->err;
+    // the states as they were
+    off = 0;
+    cudaError_t re = cudaSuccess;
+    for (int s = 0; s < b->nsys && re == cudaSuccess; s++) {
+        re = cudaMemcpyAsync(b->psi[s].p, (char *)save + off, bytes[s], cudaMemcpyDeviceToDevice, b->stream);
+        off += bytes[s];
+    }
+    if (re == cudaSuccess)
+        re = cudaStreamSynchronize(b->stream);
+    cudaFree(save);
+    if (e0)
+        cudaEventDestroy(e0);
+    if (e1)
+        cudaEventDestroy(e1);
+    if (re != cudaSuccess)
+        return bfail(b, TS_ERR_CUDA, std::string("ts_batch_autotune: restoring the states: ") + cudaGetErrorString(re));
+    if (st) {
+        ts_batch_set_schedule(b, keep_tb, keep_cb);
+        return bfail(b, st, "ts_batch_autotune: a trial failed: " + trial_err);
+    }
+    if (best_ms)
+        *best_ms = best;
+    tune_store(cache_path, gpu, key, (int)b->prec, btb, bcb, best);
+    return ts_batch_set_schedule(b, btb, bcb);
+}
+
 } // extern "C"

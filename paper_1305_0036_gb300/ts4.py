@@ -55,6 +55,8 @@ SIGNATURES = {
     "ts_batch_set_states": (_I, [_P, _I, _P, _I]),
     "ts_batch_get_states": (_I, [_P, _I, _P, _I]),
     "ts_batch_set_schedule": (_I, [_P, _I, _I]),
+    "ts_batch_get_schedule": (_I, [_P, _P, _P]),
+    "ts_batch_autotune": (_I, [_P, _D, _I, ctypes.c_char_p, _P]),
     "ts_batch_step": (_I, [_P, _D, _I64]),
     "ts_batch_observe": (_I, [_P, _I, _P]),
     "ts_batch_kernel_launches": (_I64, [_P]),
@@ -255,6 +257,19 @@ class Batch:
 
     def set_schedule(self, tile_bits=0, coalesce_bits=0):
         _bcheck(_lib.ts_batch_set_schedule(self.b, int(tile_bits), int(coalesce_bits)), self.b)
+
+    def schedule(self):
+        tb, cb = ctypes.c_int(), ctypes.c_int()
+        _bcheck(_lib.ts_batch_get_schedule(self.b, ctypes.byref(tb), ctypes.byref(cb)), self.b)
+        return {"tile_bits": tb.value, "coalesce_bits": cb.value}
+
+    def autotune(self, tau, reps=2, cache_path=None):
+        """Brute-force search of the ensemble's tile shape (library side); returns the best ms
+        per ensemble step, or -1 when the shape came from the cache file."""
+        ms = ctypes.c_double(0.0)
+        _bcheck(_lib.ts_batch_autotune(self.b, float(tau), int(reps),
+                                       cache_path.encode() if cache_path else None, ctypes.byref(ms)), self.b)
+        return ms.value
 
     def step(self, tau, nsteps=1):
         _bcheck(_lib.ts_batch_step(self.b, float(tau), int(nsteps)), self.b)
