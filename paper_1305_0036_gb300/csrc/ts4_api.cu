@@ -2048,21 +2048,18 @@ ts_status ts_autotune(ts_ctx *ctx, double tau, int reps, const char *cache_path,
             ctx->cbits = c;
             Schedule trial;
             const std::vector<HostSlot> slots = make_slots(ctx->N, 4, tau, 1);
-            st = (ts_status)cudaMemcpyAsync(ctx->scratch.p, ctx->psi.p, state_bytes(ctx), cudaMemcpyDeviceToDevice,
-                                            ctx->stream);
-            if (st) {
+            if (cudaMemcpyAsync(ctx->scratch.p, ctx->psi.p, state_bytes(ctx), cudaMemcpyDeviceToDevice,
+                                ctx->stream) != cudaSuccess) {
                 st = TS_ERR_CUDA;
                 break;
             }
             st = run_slots(ctx, trial, ctx->scratch.p, 4, tau, 1, 0, slots);   // warm-up and schedule build
-            if (!st)
-                st = (ts_status)cudaEventRecord(e0, ctx->stream);
+            if (!st && cudaEventRecord(e0, ctx->stream) != cudaSuccess)
+                st = TS_ERR_CUDA;
             for (int r = 0; r < reps && !st; r++)
                 st = run_slots(ctx, trial, ctx->scratch.p, 4, tau, 1, 0, slots);
-            if (!st)
-                st = (ts_status)cudaEventRecord(e1, ctx->stream);
-            if (!st)
-                st = (ts_status)cudaEventSynchronize(e1);
+            if (!st && (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+                st = TS_ERR_CUDA;
             float ms = 0.f;
             if (!st && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms / reps < best) {
                 best = ms / reps;
@@ -2070,8 +2067,6 @@ ts_status ts_autotune(ts_ctx *ctx, double tau, int reps, const char *cache_path,
                 bcb = c;
             }
             reset_schedule(trial, ctx->stream);
-            if (st && st != TS_ERR_CUDA && st != TS_ERR_OOM && st != TS_ERR_ARG)
-                st = TS_ERR_CUDA;
         }
     }
     cudaEventDestroy(e0);
