@@ -354,9 +354,16 @@ def run_ours(args, ws, rank, local):
         c.close()
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
         info = oracle_sample(4)
+        # the same sample on one core (one U4 step at N=20 instead of four)
+        oracle.set_num_threads(1)
+        one = oracle_sample(1)
+        oracle.set_num_threads(info["cores"])
         line["cpu_baseline"] = {"value": 1.0 / info["t_step_n28_s"], "unit": "TS4 steps/s",
-                                "cores": info["cores"], "kind": "oracle", "sample": info["sample"]}
+                                "cores": info["cores"], "kind": "oracle", "sample": info["sample"],
+                                "single_thread": {"value": 1.0 / one["t_step_n28_s"], "cores": one["cores"],
+                                                  "sample": one["sample"]}}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -67,6 +67,7 @@ def lib():
                 "oracle_apply_hamiltonian": (None, [P, P, i, P, P, P, P, P, P]),
                 "oracle_energy": (d, [P, i, P, P, P, P, P, P]),
                 "oracle_num_threads": (i, []),
+                "oracle_set_num_threads": (None, [i]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -199,3 +200,8 @@ def energy(psi, H: Hamiltonian):
 
 def num_threads() -> int:
     return int(lib().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (for timing it on one core)."""
+    lib().oracle_set_num_threads(int(n))
