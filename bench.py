@@ -46,8 +46,8 @@ def kernel_source_hash():
 
 
 def measured_traffic(N):
-    """DRAM bytes per k_tile launch from the committed ncu summary, scaled to 2^N amplitudes;
-    None when the kernel sources changed since the counters were taken."""
+    """DRAM bytes per complex64 k_tile launch from the committed ncu summary, scaled to 2^N
+    amplitudes; None when the kernel sources changed since the counters were taken."""
     try:
         kv = {}
         with open(TRAFFIC_FILE) as f:
@@ -316,7 +316,7 @@ def run_ours(args, ws, rank, local):
         "hbm": {"effective_gbs": eff_gbs, "effective_frac": eff_gbs / peak,
                 "pass_traffic_gbs": dram_gbs, "pass_traffic_frac": dram_gbs / peak},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": measured_traffic(N), "peak_kind": peak_kind,
+                     "frac": achieved / peak, "traffic": measured_traffic(N) if prec == "c64" else None, "peak_kind": peak_kind,
                      "kernel": "k_tile", "alg_bytes_per_launch": alg_bytes_launch,
                      "avg_launch_ms": avg_pass_ms},
         "e2e": {"value": e2e_value, "unit": "TS4 steps/s", "h2d_bytes_per_step": state_bytes / args.steps,
