@@ -330,7 +330,11 @@ def test_config3_echo_c64_and_c128(ts4):
 
 
 def test_config5_n33_capacity_ising_and_norm(ts4):
-    """N=33 complex64 (68.7 GB, in place): Ising closed form on samples and norm of the XYZ run."""
+    """N=33 complex64 (68.7 GB, in place, 64-bit indices and offsets): norm and S^z bounds of
+    the XYZ run, then the Ising closed form on the Neel basis state.  With J^x = J^y = 0 every
+    rotation layer still runs, and they compose to the identity, so the state must come back
+    to the Neel state times exp(-i n tau E_z(Neel)); the overlap with the saved reference
+    (a second 68.7 GB buffer) checks both the phase and that no amplitude leaked."""
     s = W.xyz_chain(33, 1.0, 0.8, 0.5, h=0.1)
     N = s.N
     neel = W.neel_index(N)
@@ -341,6 +345,17 @@ def test_config5_n33_capacity_ising_and_norm(ts4):
     sz = ctx.sz()
     assert np.all(np.abs(sz) <= 0.5 + 1e-6)
     ctx.close()
+    z = np.zeros_like(s.Jz)
+    ising = ts4.Context(N, z, z, s.Jz, s.hz, prec="c64")
+    ising.set_basis_state(neel)
+    ising.save_reference()
+    n, tau = 2, 0.02
+    ising.step(tau, n)
+    sig = 2.0 * ((neel >> np.arange(N)) & 1) - 1.0
+    E = sig @ np.triu(s.Jz, 1) @ sig / 4 + sig @ s.hz / 2
+    ov = ising.overlap()
+    assert abs(ov - np.exp(-1j * n * tau * E)) <= 20 * n * (N + 8) * U32, (ov, E)
+    ising.close()
 
 
 # ------------------------------------------------------------------ error paths
