@@ -358,6 +358,21 @@ def test_config5_n33_capacity_ising_and_norm(ts4):
     ising.close()
 
 
+def test_largest_size_n34_c64(ts4):
+    """N=34, the largest size the library accepts: a 137 GB complex64 state (half of GB300's
+    HBM).  One TS4 step of the XYZ chain from the Neel state keeps the norm."""
+    import torch
+    torch.cuda.empty_cache()
+    s = W.xyz_chain(34, 1.0, 0.8, 0.5, h=0.1)
+    ctx = ts4.Context.from_system(s, prec="c64")
+    ctx.set_basis_state(W.neel_index(34))
+    ctx.step(0.02, 1)
+    assert ctx.schedule()["groups"] == 4
+    assert abs(ctx.norm() - 1.0) <= 1e-5
+    ctx.close()
+    torch.cuda.empty_cache()
+
+
 # ------------------------------------------------------------------ error paths
 
 def test_error_paths(ts4):
