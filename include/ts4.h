@@ -206,6 +206,38 @@ TS4_API double ts_step_bound(const ts_ctx *ctx);
 TS4_API uint64_t ts_tile_global_index(int N, int c, int w, int h, uint64_t f, uint64_t e);
 
 /*
+ * The fused-pass plan, computed on the host without a GPU (Secs. 3.3-3.4: the bit
+ * groups and the order in which one pass per group applies the rotation layers and
+ * the diagonal slots of Sec. 2).  For nsteps chained steps of the given order
+ * (1, 2 or 4) at N spins with the given tile and coalescing bits (0 = defaults) and
+ * precision (which fixes the register bits of a tile):
+ *   groups[i]  the bit groups: the tile holds global bits [0, c) and [w, w + h);
+ *              group 0 is the TB lowest spins (c = 0);
+ *   passes[p]  per kernel launch, in launch order: its group, the slot it applies
+ *              (index into the slot list, -1 for none), and the global spins it
+ *              rotates before and after the slot (rot_before holds every rotation of
+ *              a pass without a slot); dup = 1 if some spin would be rotated twice on
+ *              the same side of the slot (never, for a valid plan).
+ * The slot list of an isolated run has layers + 1 entries (20 layers per TS4 step,
+ * 4 per U2 step, 3 per U1 step).  Arrays are caller-owned; at most max_groups /
+ * max_passes entries are written, the counts are always returned (call with NULL
+ * arrays and 0 to size them).
+ * Errors: TS_ERR_ARG (N outside [1, 34], N smaller than the tile, an unsupported
+ * tile or coalescing width, order not 1, 2 or 4, nsteps < 1, NULL counts).
+ */
+typedef struct { int c, w, h; } ts_plan_group;
+typedef struct {
+    int group;
+    int slot;
+    uint64_t rot_before;
+    uint64_t rot_after;
+    int dup;
+} ts_plan_pass;
+TS4_API ts_status ts_plan(int N, ts_prec prec, int tile_bits, int coalesce_bits, int order, int64_t nsteps,
+                          ts_plan_group *groups, int max_groups, int *ngroups, ts_plan_pass *passes,
+                          int64_t max_passes, int64_t *npasses);
+
+/*
  * The paper's phase-table mode (Sec. 3.1: the energies of every basis state are
  * precomputed once and each phase reads them), kept for an A/B comparison with
  * the bit-test slots.  enable != 0 builds three tables E_x, E_y, E_z of 2^N

@@ -1159,6 +1159,54 @@ uint64_t ts_tile_global_index(int N, int c, int w, int h, uint64_t f, uint64_t e
     return tile_global_index(c, w, h, f, e);
 }
 
+ts_status ts_plan(int N, ts_prec prec, int tile_bits, int coalesce_bits, int order, int64_t nsteps,
+                  ts_plan_group *groups, int max_groups, int *ngroups, ts_plan_pass *passes, int64_t max_passes,
+                  int64_t *npasses)
+{
+    if (!ngroups || !npasses || N < 1 || N > kMaxN || (prec != TS_C64 && prec != TS_C128) ||
+        (order != 1 && order != 2 && order != 4) || nsteps < 1)
+        return TS_ERR_ARG;
+    const int TB = tile_bits ? tile_bits : default_tile(prec);
+    const int RB = reg_bits(prec);
+    const int cb = coalesce_bits ? coalesce_bits : default_cbits(prec);
+    if (!tile_supported(prec, TB) || N < TB || cb < 1 || cb > TB - RB)
+        return TS_ERR_ARG;
+    const std::vector<Group> G = make_groups(N, TB, cb);
+    const int64_t L = (int64_t)make_slots(N, order, 0.01, nsteps).size() - 1;
+    const std::vector<HostPass> P = make_passes(G, L, TB, RB);
+    *ngroups = (int)G.size();
+    *npasses = (int64_t)P.size();
+    for (int i = 0; i < (int)G.size() && groups && i < max_groups; i++)
+        groups[i] = ts_plan_group{G[i].c, G[i].w, G[i].h};
+    for (int64_t p = 0; p < (int64_t)P.size() && passes && p < max_passes; p++) {
+        const HostPass &hp = P[(size_t)p];
+        const Group &g = G[(size_t)hp.group];
+        uint64_t side[2] = {0, 0};
+        int dup = 0, after = 0;
+        // register bits [lo, hi) of chunk k: tile-local bits W_k + b, W_k = min(k RB, TB - RB)
+        auto rotate = [&](int k, int lo, int hi) {
+            const int W = (k * RB < TB - RB) ? k * RB : TB - RB;
+            for (int b = lo; b < hi; b++) {
+                const int l = W + b;                               // tile-local bit
+                const int pos = l < g.h ? g.w + l : l - g.h;       // global spin
+                const uint64_t m = UINT64_C(1) << pos;
+                if (side[after] & m)
+                    dup = 1;
+                side[after] |= m;
+            }
+        };
+        for (int s = 0; s < hp.nsteps; s++) {
+            const StepDesc &d = hp.steps[s];
+            rotate(d.k, d.r0lo, d.r0hi);
+            if (d.ph)
+                after = 1;
+            rotate(d.k, d.r1lo, d.r1hi);
+        }
+        passes[p] = ts_plan_pass{hp.group, hp.slot, side[0], side[1], dup};
+    }
+    return TS_OK;
+}
+
 ts_status ts_create(ts_ctx **out, int N, const double *Jx, const double *Jy, const double *Jz, const double *h,
                     ts_prec prec, void *cuda_stream)
 {

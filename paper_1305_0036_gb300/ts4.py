@@ -46,6 +46,7 @@ SIGNATURES = {
     "ts_get_schedule": (_I, [_P, _P, _P, _P, _P, _P]),
     "ts_step_bound": (_D, [_P]),
     "ts_tile_global_index": (_U64, [_I, _I, _I, _I, _U64, _U64]),
+    "ts_plan": (_I, [_I, _I, _I, _I, _I, _I64, _P, _I, _P, _P, _I64, _P]),
     "ts_kernel_launches": (_I64, [_P]),
     "ts_reduce_sz_static": (_I, [_P, _I, _I, _P, _P]),
     "ts_autotune": (_I, [_P, _D, _I, ctypes.c_char_p, _P]),
@@ -177,6 +178,33 @@ def ts_step_bound(ctx):
 
 def ts_tile_global_index(N, c, w, h, f, e):
     return int(_lib.ts_tile_global_index(int(N), int(c), int(w), int(h), int(f), int(e)))
+
+
+class PlanGroup(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_int), ("w", ctypes.c_int), ("h", ctypes.c_int)]
+
+
+class PlanPass(ctypes.Structure):
+    _fields_ = [("group", ctypes.c_int), ("slot", ctypes.c_int), ("rot_before", ctypes.c_uint64),
+                ("rot_after", ctypes.c_uint64), ("dup", ctypes.c_int)]
+
+
+def ts_plan(N, prec=TS_C64, tile_bits=0, coalesce_bits=0, order=4, nsteps=1):
+    """The fused-pass plan (host only, no GPU): a list of group dicts and a list of pass dicts."""
+    ng, npass = ctypes.c_int(), ctypes.c_int64()
+    st = _lib.ts_plan(int(N), int(prec), int(tile_bits), int(coalesce_bits), int(order), int(nsteps),
+                      None, 0, ctypes.byref(ng), None, 0, ctypes.byref(npass))
+    if st:
+        raise TS4Error(st, "ts_plan: invalid arguments")
+    G = (PlanGroup * max(ng.value, 1))()
+    P = (PlanPass * max(npass.value, 1))()
+    _check(_lib.ts_plan(int(N), int(prec), int(tile_bits), int(coalesce_bits), int(order), int(nsteps),
+                        ctypes.cast(G, _P), ng.value, ctypes.byref(ng), ctypes.cast(P, _P), npass.value,
+                        ctypes.byref(npass)), None)
+    groups = [dict(c=g.c, w=g.w, h=g.h) for g in G[:ng.value]]
+    passes = [dict(group=p.group, slot=p.slot, rot_before=int(p.rot_before), rot_after=int(p.rot_after),
+                   dup=p.dup) for p in P[:npass.value]]
+    return groups, passes
 
 
 def ts_kernel_launches(ctx):
