@@ -154,6 +154,26 @@ TS4_API ts_status ts_step(ts_ctx *ctx, double tau, int64_t nsteps);
 TS4_API ts_status ts_step_order(ts_ctx *ctx, int order, double tau, int64_t nsteps);
 
 /*
+ * Chaining of consecutive ts_step calls (Sec. 2: the final P_z half of one U2 and the first of
+ * the next merge into one slot).  With enable != 0, each ts_step / ts_step_order of order 2
+ * or 4 on the fused kernel holds back its final pass (the last layer's rotation of one bit
+ * group and the closing P_z slot); the next step call runs it inside its own first pass, so
+ * a loop of one-step calls costs what one chained call costs (20 (g - 1) passes per TS4 step
+ * instead of 20 (g - 1) + 1).  While a pass is held back, the state buffer does not yet hold
+ * the evolved state: ts_get_state, ts_observe (all but TS_NORM, whose value accounts for
+ * the held-back pass exactly: a Walsh-Hadamard gain and a slot scale), ts_save_reference,
+ * ts_set_schedule, ts_set_transverse_fields, ts_autotune and ts_flush run it first;
+ * ts_set_state, ts_set_basis_state and binding a new state buffer drop it.  Callers that
+ * read a bound state buffer directly call ts_flush first.  enable = 0 (the default) runs
+ * any held-back pass and turns chaining off.
+ * Errors: TS_ERR_ARG (NULL context), TS_ERR_CUDA.
+ */
+TS4_API ts_status ts_set_chaining(ts_ctx *ctx, int enable);
+
+/* Runs a held-back final pass (see ts_set_chaining), if any.  Errors: TS_ERR_ARG, TS_ERR_CUDA. */
+TS4_API ts_status ts_flush(ts_ctx *ctx);
+
+/*
  * Evaluates an observable (TS_NORM, TS_ENERGY, TS_SZ, TS_ECHO, TS_OVERLAP)
  * into host memory `out` (sizes above).  Sums are accumulated in FP64.
  * Synchronises the context's stream.  TS_ECHO/TS_OVERLAP without a saved

@@ -74,6 +74,8 @@ struct Schedule {
     double tau = 0.0;
     int64_t n = -1;
     int kernel = -1, TB = 0, cbits = 0, slot0_pcq = -1, mode = 0;
+    int shape = 0;        // SHAPE_* flags: how the pass list differs from make_passes
+    int tail_group = 0;   // SHAPE_TAIL_ONLY: the group of the single pass
     // content
     std::vector<HostSlot> slots;
     std::vector<Group> groups;
@@ -145,6 +147,16 @@ struct ts_ctx {
     int TB = 0, RB = 0, cbits = 0;
     Schedule sched;       // last ts_step schedule
     Schedule sched_obs;   // frame rotation used by TS_ENERGY
+    // The final pass of the last ts_step (the last layer's rotation of group tail_group, then
+    // the P_z slot tail_slot), held back so that the next ts_step runs it inside its first
+    // pass, as a chained run does; any use of the state other than the next step or the norm
+    // runs it first (flush_tail).
+    bool chain = false;   // ts_set_chaining: hold back the final pass of each ts_step
+    bool tail_pending = false;
+    HostSlot tail_slot;
+    int tail_group = 0;
+    int tail_h = 0;       // spins that rotation covers: the norm grows by 2^tail_h through it
+    Schedule sched_tail;  // that pass alone
     std::string err;
     int64_t launches = 0;
 };
@@ -746,6 +758,30 @@ ts_status run_basic(ts_ctx *ctx, void *buf, const std::vector<HostSlot> &slots)
 
 // Builds the fused schedule for the slots in S: groups, passes, per-group I/O
 // layouts, and one table per distinct (slot values, group, phase chunk).
+// Pass-list shapes: the first pass also completes the previous call's last layer on its
+// group (the slot is then the merged P_z of both calls); the last pass is held back; or the
+// held-back pass alone.
+enum { SHAPE_HEAD_MERGED = 1, SHAPE_TAIL_DEFERRED = 2, SHAPE_TAIL_ONLY = 4 };
+
+// Two consecutive P_z slots as one (Sec. 2: P_z(a) P_z(b) = P_z(a + b)); the scale and the
+// powers of i multiply as well.
+HostSlot merge_z(const HostSlot &a, const HostSlot &b)
+{
+    HostSlot m = b;
+    m.t = a.t + b.t;
+    m.th0 = a.th0 + b.th0;
+    m.pcq = (a.pcq + b.pcq) & 3;
+    m.scale_exp = a.scale_exp + b.scale_exp;
+    m.mag = a.mag * b.mag;
+    return m;
+}
+
+bool same_slot(const HostSlot &a, const HostSlot &b)
+{
+    return a.t == b.t && a.th0 == b.th0 && a.mag == b.mag && a.alpha == b.alpha && a.pcq == b.pcq &&
+           a.scale_exp == b.scale_exp;
+}
+
 ts_status prepare_fused(ts_ctx *ctx, Schedule &S)
 {
     const int RB = ctx->RB, TB = ctx->TB;
@@ -773,6 +809,16 @@ ts_status prepare_fused(ts_ctx *ctx, Schedule &S)
     }
     const int64_t L = (int64_t)S.slots.size() - 1;
     S.passes = make_passes(S.groups, L, TB, RB);
+    if (S.shape & SHAPE_TAIL_ONLY) {
+        S.passes.assign(1, make_pass(S.tail_group, S.groups[(size_t)S.tail_group], P_ROT_PHASE, 0, TB, RB));
+    } else {
+        if (S.shape & SHAPE_HEAD_MERGED) {
+            const int g0 = S.passes.front().group;
+            S.passes.front() = make_pass(g0, S.groups[(size_t)g0], P_ROT_PHASE_ROT, 0, TB, RB);
+        }
+        if (S.shape & SHAPE_TAIL_DEFERRED)
+            S.passes.pop_back();
+    }
     S.tab_size = tab_size(ctx->prec, TB);
     std::map<std::tuple<double, int, int, int, int>, int> seen;
     S.tabs.clear();
@@ -929,7 +975,7 @@ bool fused_usable(const ts_ctx *ctx) { return ctx->kernel == TS_KERNEL_FUSED && 
 // Runs the layers of `slots` on buf with the selected kernel.  The schedule is
 // cached under `key` so that repeated calls reuse the pass list and tables.
 ts_status run_slots(ts_ctx *ctx, Schedule &S, void *buf, int order, double tau, int64_t n, int mode,
-                    const std::vector<HostSlot> &slots)
+                    const std::vector<HostSlot> &slots, int shape = 0, int tail_group = 0)
 {
     // small N: the fused kernel needs a full tile; take the largest provided tile <= N
     const int keepTB = ctx->TB;
@@ -940,7 +986,8 @@ ts_status run_slots(ts_ctx *ctx, Schedule &S, void *buf, int order, double tau, 
         st = run_basic(ctx, buf, slots);
     } else {
         const bool hit = S.order == order && S.tau == tau && S.n == n && S.kernel == ctx->kernel &&
-                         S.TB == ctx->TB && S.cbits == ctx->cbits && S.mode == mode;
+                         S.TB == ctx->TB && S.cbits == ctx->cbits && S.mode == mode && S.shape == shape &&
+                         S.tail_group == tail_group && !S.slots.empty() && same_slot(S.slots[0], slots[0]);
         if (!hit) {
             // keep the device table buffer for reuse, rebuild everything else
             void *keep = S.dtab;
@@ -957,8 +1004,12 @@ ts_status run_slots(ts_ctx *ctx, Schedule &S, void *buf, int order, double tau, 
             S.dmap = keep_map;
             S.dmap_cap = keep_map_cap;
             S.slots = slots;
+            S.shape = shape;
+            S.tail_group = tail_group;
             st = prepare_fused(ctx, S);
             if (st == TS_OK) {
+                S.shape = shape;
+                S.tail_group = tail_group;
                 S.order = order;
                 S.tau = tau;
                 S.n = n;
@@ -975,6 +1026,16 @@ ts_status run_slots(ts_ctx *ctx, Schedule &S, void *buf, int order, double tau, 
     }
     ctx->TB = keepTB;
     return st;
+}
+
+// Runs the held-back final pass of the last ts_step (if any) on the state.
+ts_status flush_tail(ts_ctx *ctx)
+{
+    if (!ctx->tail_pending)
+        return TS_OK;
+    ctx->tail_pending = false;
+    const std::vector<HostSlot> one(1, ctx->tail_slot);
+    return run_slots(ctx, ctx->sched_tail, ctx->psi.p, 0, 0.0, 0, 0, one, SHAPE_TAIL_ONLY, ctx->tail_group);
 }
 
 // ------------------------------------------------------------ reductions
@@ -1277,6 +1338,9 @@ ts_status ts_set_transverse_fields(ts_ctx *ctx, const double *hx, const double *
     const int N = ctx->N;
     if ((hx && !finite_all(hx, N)) || (hy && !finite_all(hy, N)))
         return fail(ctx, TS_ERR_ARG, "ts_set_transverse_fields: non-finite field");
+    const ts_status fst = flush_tail(ctx);   // the held-back slot belongs to the old H
+    if (fst)
+        return fst;
     for (int i = 0; i < N; i++) {
         ctx->hraw[0][i] = hx ? hx[i] : 0.0;
         ctx->hraw[1][i] = hy ? hy[i] : 0.0;
@@ -1288,6 +1352,7 @@ ts_status ts_set_transverse_fields(ts_ctx *ctx, const double *hx, const double *
     TS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     reset_schedule(ctx->sched, ctx->stream);
     reset_schedule(ctx->sched_obs, ctx->stream);
+    reset_schedule(ctx->sched_tail, ctx->stream);
     if (ctx->dE) {   // the phase tables hold the old fields: rebuild them
         ts_set_phase_tables(ctx, 0);
         return ts_set_phase_tables(ctx, 1);
@@ -1306,6 +1371,8 @@ ts_status ts_bind_buffers(ts_ctx *ctx, void *psi, void *ref, void *scratch, size
     for (void *p : {psi, ref, scratch})
         if (p && ((uintptr_t)p & 255))
             return fail(ctx, TS_ERR_ARG, "ts_bind_buffers: buffer not 256-byte aligned");
+    if (psi != ctx->psi.p)
+        ctx->tail_pending = false;
     free_buf(ctx->psi);
     ctx->psi.p = psi;
     if (ref) {
@@ -1327,6 +1394,7 @@ ts_status ts_set_state(ts_ctx *ctx, const void *amps, int on_device)
     ts_status st = ensure_buf(ctx, ctx->psi, "state buffer");
     if (st)
         return st;
+    ctx->tail_pending = false;
     TS_CUDA(ctx, cudaMemcpyAsync(ctx->psi.p, amps, state_bytes(ctx),
                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     if (!on_device)
@@ -1343,6 +1411,7 @@ ts_status ts_set_basis_state(ts_ctx *ctx, uint64_t s)
     ts_status st = ensure_buf(ctx, ctx->psi, "state buffer");
     if (st)
         return st;
+    ctx->tail_pending = false;
     const unsigned g = grid_for(ctx, dim_of(ctx), 256);
     if (ctx->prec == TS_C64)
         k_set_basis<float2><<<g, 256, 0, ctx->stream>>>((float2 *)ctx->psi.p, dim_of(ctx), s);
@@ -1359,7 +1428,10 @@ ts_status ts_save_reference(ts_ctx *ctx)
         return TS_ERR_ARG;
     if (!ctx->psi.p)
         return fail(ctx, TS_ERR_STATE, "ts_save_reference: no state set");
-    ts_status st = ensure_buf(ctx, ctx->ref, "reference buffer");
+    ts_status st = flush_tail(ctx);
+    if (st)
+        return st;
+    st = ensure_buf(ctx, ctx->ref, "reference buffer");
     if (st)
         return st;
     TS_CUDA(ctx, cudaMemcpyAsync(ctx->ref.p, ctx->psi.p, state_bytes(ctx), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1377,11 +1449,58 @@ ts_status ts_step_order(ts_ctx *ctx, int order, double tau, int64_t nsteps)
         return fail(ctx, TS_ERR_STATE, "ts_step: no state set");
     if (nsteps == 0)
         return TS_OK;
-    const std::vector<HostSlot> slots = make_slots(ctx->N, order, tau, nsteps);
-    return run_slots(ctx, ctx->sched, ctx->psi.p, order, tau, nsteps, 0, slots);
+    std::vector<HostSlot> slots = make_slots(ctx->N, order, tau, nsteps);
+    // With chaining on, consecutive calls run like one chained call (Sec. 2: the P_z halves of
+    // adjacent U2s merge): a held-back final pass of the previous call is merged into this
+    // call's first pass, and with an even number of layers (orders 2 and 4) this call's final
+    // pass is held back in turn.  Both ends of such a run sit on the first group of the zigzag.
+    const bool fused = fused_usable(ctx);
+    std::vector<Group> G;
+    if (fused)
+        G = make_groups(ctx->N, ctx->TB, ctx->cbits);
+    const int ng = (int)G.size();
+    const int first = ng >= 3 ? 1 : 0;
+    int shape = 0;
+    if (ctx->tail_pending) {
+        if (fused && ng >= 2 && ctx->tail_group == first) {
+            slots[0] = merge_z(ctx->tail_slot, slots[0]);
+            shape |= SHAPE_HEAD_MERGED;
+            ctx->tail_pending = false;
+        } else {
+            const ts_status fst = flush_tail(ctx);
+            if (fst)
+                return fst;
+        }
+    }
+    const bool defer = ctx->chain && fused && ng >= 2 && (order == 2 || order == 4);
+    if (defer)
+        shape |= SHAPE_TAIL_DEFERRED;
+    const ts_status st = run_slots(ctx, ctx->sched, ctx->psi.p, order, tau, nsteps, 0, slots, shape, 0);
+    if (st == TS_OK && defer) {
+        ctx->tail_pending = true;
+        ctx->tail_slot = slots.back();
+        ctx->tail_group = first;
+        ctx->tail_h = G[(size_t)first].h;
+    }
+    return st;
 }
 
 ts_status ts_step(ts_ctx *ctx, double tau, int64_t nsteps) { return ts_step_order(ctx, 4, tau, nsteps); }
+
+ts_status ts_set_chaining(ts_ctx *ctx, int enable)
+{
+    if (!ctx)
+        return TS_ERR_ARG;
+    ctx->chain = enable != 0;
+    return enable ? TS_OK : flush_tail(ctx);
+}
+
+ts_status ts_flush(ts_ctx *ctx)
+{
+    if (!ctx)
+        return TS_ERR_ARG;
+    return flush_tail(ctx);
+}
 
 ts_status ts_observe(ts_ctx *ctx, int what, double *out)
 {
@@ -1391,6 +1510,19 @@ ts_status ts_observe(ts_ctx *ctx, int what, double *out)
         return fail(ctx, TS_ERR_STATE, "ts_observe: no state set");
     const int N = ctx->N;
     ts_status st = TS_OK;
+    if (what == TS_NORM) {
+        // a held-back pass is a Walsh-Hadamard rotation of tail_h spins (norm x 2^tail_h, the
+        // butterflies are unnormalised) and a diagonal slot of modulus mag 2^-scale_exp
+        st = sum_norm(ctx, ctx->psi.p, out);
+        if (st == TS_OK && ctx->tail_pending) {
+            const double m = std::ldexp(ctx->tail_slot.mag, -ctx->tail_slot.scale_exp);
+            out[0] *= std::ldexp(m * m, ctx->tail_h);
+        }
+        return st;
+    }
+    st = flush_tail(ctx);
+    if (st)
+        return st;
     switch (what) {
     case TS_NORM:
         return sum_norm(ctx, ctx->psi.p, out);
@@ -1471,6 +1603,9 @@ ts_status ts_get_state(ts_ctx *ctx, void *amps, int on_device)
         return ctx ? fail(ctx, TS_ERR_ARG, "ts_get_state: NULL destination") : TS_ERR_ARG;
     if (!ctx->psi.p)
         return fail(ctx, TS_ERR_STATE, "ts_get_state: no state set");
+    const ts_status fst = flush_tail(ctx);
+    if (fst)
+        return fst;
     TS_CUDA(ctx, cudaMemcpyAsync(amps, ctx->psi.p, state_bytes(ctx),
                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
     if (!on_device)
@@ -1494,6 +1629,7 @@ ts_status ts_destroy(ts_ctx *ctx)
         cudaFree(ctx->dpart);
     release_tables(ctx->sched, ctx->stream);
     release_tables(ctx->sched_obs, ctx->stream);
+    release_tables(ctx->sched_tail, ctx->stream);
     if (ctx->hout)
         cudaFreeHost(ctx->hout);
     if (ctx->dE)
@@ -1546,11 +1682,15 @@ ts_status ts_set_schedule(ts_ctx *ctx, int kernel, int tile_bits, int coalesce_b
         return fail(ctx, TS_ERR_ARG, "ts_set_schedule: tile size not provided for this precision");
     if (cb < 1 || cb > tb - ctx->RB)
         return fail(ctx, TS_ERR_ARG, "ts_set_schedule: coalescing bits must be in [1, tile_bits - reg_bits]");
+    const ts_status fst = flush_tail(ctx);   // the held-back pass uses the current tiles
+    if (fst)
+        return fst;
     ctx->kernel = kernel;
     ctx->TB = tb;
     ctx->cbits = cb;
     reset_schedule(ctx->sched, ctx->stream);
     reset_schedule(ctx->sched_obs, ctx->stream);
+    reset_schedule(ctx->sched_tail, ctx->stream);
     return TS_OK;
 }
 
@@ -2066,6 +2206,9 @@ ts_status ts_autotune(ts_ctx *ctx, double tau, int reps, const char *cache_path,
         return ctx ? fail(ctx, TS_ERR_ARG, "ts_autotune: tau must be finite and reps >= 1") : TS_ERR_ARG;
     if (!ctx->psi.p)
         return fail(ctx, TS_ERR_STATE, "ts_autotune: no state set");
+    const ts_status fst = flush_tail(ctx);   // the tile shape may change
+    if (fst)
+        return fst;
     const std::string gpu = device_name();
     int tb = 0, cb = 0;
     if (tune_lookup(cache_path, gpu, ctx->N, (int)ctx->prec, &tb, &cb) && tile_supported(ctx->prec, tb) &&

@@ -47,6 +47,8 @@ SIGNATURES = {
     "ts_step_bound": (_D, [_P]),
     "ts_tile_global_index": (_U64, [_I, _I, _I, _I, _U64, _U64]),
     "ts_plan": (_I, [_I, _I, _I, _I, _I, _I64, _P, _I, _P, _P, _I64, _P]),
+    "ts_set_chaining": (_I, [_P, _I]),
+    "ts_flush": (_I, [_P]),
     "ts_kernel_launches": (_I64, [_P]),
     "ts_reduce_sz_static": (_I, [_P, _I, _I, _P, _P]),
     "ts_autotune": (_I, [_P, _D, _I, ctypes.c_char_p, _P]),
@@ -395,6 +397,14 @@ class Context:
 
     def step(self, tau, nsteps=1):
         ts_step(self.ctx, tau, nsteps)
+
+    def set_chaining(self, enable=True):
+        """Hold back the final pass of each step call until the next one (library side)."""
+        _check(_lib.ts_set_chaining(self.ctx, 1 if enable else 0), self.ctx)
+
+    def flush(self):
+        """Run a held-back final pass, so that the bound state buffer holds the state."""
+        _check(_lib.ts_flush(self.ctx), self.ctx)
 
     def step_order(self, order, tau, nsteps=1):
         ts_step_order(self.ctx, order, tau, nsteps)
