@@ -239,11 +239,15 @@ TS4_API uint64_t ts_tile_global_index(int N, int c, int w, int h, uint64_t f, ui
  *              a pass without a slot); dup = 1 if some spin would be rotated twice on
  *              the same side of the slot (never, for a valid plan).
  * The slot list of an isolated run has layers + 1 entries (20 layers per TS4 step,
- * 4 per U2 step, 3 per U1 step).  Arrays are caller-owned; at most max_groups /
+ * 4 per U2 step, 3 per U1 step).  chain (see ts_set_chaining): bit 1 = the call
+ * continues a held-back pass of the previous call (its first pass then also rotates
+ * its group before its slot 0, the merged P_z); bit 2 = the call holds back its final
+ * pass (the plan omits it).  chain != 0 needs at least two bit groups.  Arrays are caller-owned; at most max_groups /
  * max_passes entries are written, the counts are always returned (call with NULL
  * arrays and 0 to size them).
  * Errors: TS_ERR_ARG (N outside [1, 34], N smaller than the tile, an unsupported
- * tile or coalescing width, order not 1, 2 or 4, nsteps < 1, NULL counts).
+ * tile or coalescing width, order not 1, 2 or 4, nsteps < 1, chain outside [0, 3] or
+ * chain with one group, NULL counts).
  */
 typedef struct { int c, w, h; } ts_plan_group;
 typedef struct {
@@ -254,7 +258,7 @@ typedef struct {
     int dup;
 } ts_plan_pass;
 TS4_API ts_status ts_plan(int N, ts_prec prec, int tile_bits, int coalesce_bits, int order, int64_t nsteps,
-                          ts_plan_group *groups, int max_groups, int *ngroups, ts_plan_pass *passes,
+                          int chain, ts_plan_group *groups, int max_groups, int *ngroups, ts_plan_pass *passes,
                           int64_t max_passes, int64_t *npasses);
 
 /*

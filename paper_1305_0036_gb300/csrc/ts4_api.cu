@@ -776,6 +776,25 @@ HostSlot merge_z(const HostSlot &a, const HostSlot &b)
     return m;
 }
 
+// make_passes with a shape applied: the held-back pass alone; or the first pass also running
+// the previous call's held-back rotation before its (merged) slot; and/or the last pass held back.
+std::vector<HostPass> shaped_passes(const std::vector<Group> &G, int64_t L, int TB, int RB, int shape,
+                                    int tail_group)
+{
+    std::vector<HostPass> P = make_passes(G, L, TB, RB);
+    if (shape & SHAPE_TAIL_ONLY) {
+        P.assign(1, make_pass(tail_group, G[(size_t)tail_group], P_ROT_PHASE, 0, TB, RB));
+        return P;
+    }
+    if (shape & SHAPE_HEAD_MERGED) {
+        const int g0 = P.front().group;
+        P.front() = make_pass(g0, G[(size_t)g0], P_ROT_PHASE_ROT, 0, TB, RB);
+    }
+    if (shape & SHAPE_TAIL_DEFERRED)
+        P.pop_back();
+    return P;
+}
+
 bool same_slot(const HostSlot &a, const HostSlot &b)
 {
     return a.t == b.t && a.th0 == b.th0 && a.mag == b.mag && a.alpha == b.alpha && a.pcq == b.pcq &&
@@ -808,17 +827,7 @@ ts_status prepare_fused(ts_ctx *ctx, Schedule &S)
         }
     }
     const int64_t L = (int64_t)S.slots.size() - 1;
-    S.passes = make_passes(S.groups, L, TB, RB);
-    if (S.shape & SHAPE_TAIL_ONLY) {
-        S.passes.assign(1, make_pass(S.tail_group, S.groups[(size_t)S.tail_group], P_ROT_PHASE, 0, TB, RB));
-    } else {
-        if (S.shape & SHAPE_HEAD_MERGED) {
-            const int g0 = S.passes.front().group;
-            S.passes.front() = make_pass(g0, S.groups[(size_t)g0], P_ROT_PHASE_ROT, 0, TB, RB);
-        }
-        if (S.shape & SHAPE_TAIL_DEFERRED)
-            S.passes.pop_back();
-    }
+    S.passes = shaped_passes(S.groups, L, TB, RB, S.shape, S.tail_group);
     S.tab_size = tab_size(ctx->prec, TB);
     std::map<std::tuple<double, int, int, int, int>, int> seen;
     S.tabs.clear();
@@ -1220,12 +1229,12 @@ uint64_t ts_tile_global_index(int N, int c, int w, int h, uint64_t f, uint64_t e
     return tile_global_index(c, w, h, f, e);
 }
 
-ts_status ts_plan(int N, ts_prec prec, int tile_bits, int coalesce_bits, int order, int64_t nsteps,
+ts_status ts_plan(int N, ts_prec prec, int tile_bits, int coalesce_bits, int order, int64_t nsteps, int chain,
                   ts_plan_group *groups, int max_groups, int *ngroups, ts_plan_pass *passes, int64_t max_passes,
                   int64_t *npasses)
 {
     if (!ngroups || !npasses || N < 1 || N > kMaxN || (prec != TS_C64 && prec != TS_C128) ||
-        (order != 1 && order != 2 && order != 4) || nsteps < 1)
+        (order != 1 && order != 2 && order != 4) || nsteps < 1 || chain < 0 || chain > 3)
         return TS_ERR_ARG;
     const int TB = tile_bits ? tile_bits : default_tile(prec);
     const int RB = reg_bits(prec);
@@ -1233,8 +1242,12 @@ ts_status ts_plan(int N, ts_prec prec, int tile_bits, int coalesce_bits, int ord
     if (!tile_supported(prec, TB) || N < TB || cb < 1 || cb > TB - RB)
         return TS_ERR_ARG;
     const std::vector<Group> G = make_groups(N, TB, cb);
+    if (chain && G.size() < 2)
+        return TS_ERR_ARG;
     const int64_t L = (int64_t)make_slots(N, order, 0.01, nsteps).size() - 1;
-    const std::vector<HostPass> P = make_passes(G, L, TB, RB);
+    // chain bit 1: the call continues a held-back pass; bit 2: it holds back its final pass
+    const int shape = ((chain & 1) ? SHAPE_HEAD_MERGED : 0) | ((chain & 2) ? SHAPE_TAIL_DEFERRED : 0);
+    const std::vector<HostPass> P = shaped_passes(G, L, TB, RB, shape, 0);
     *ngroups = (int)G.size();
     *npasses = (int64_t)P.size();
     for (int i = 0; i < (int)G.size() && groups && i < max_groups; i++)

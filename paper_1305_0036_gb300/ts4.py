@@ -46,7 +46,7 @@ SIGNATURES = {
     "ts_get_schedule": (_I, [_P, _P, _P, _P, _P, _P]),
     "ts_step_bound": (_D, [_P]),
     "ts_tile_global_index": (_U64, [_I, _I, _I, _I, _U64, _U64]),
-    "ts_plan": (_I, [_I, _I, _I, _I, _I, _I64, _P, _I, _P, _P, _I64, _P]),
+    "ts_plan": (_I, [_I, _I, _I, _I, _I, _I64, _I, _P, _I, _P, _P, _I64, _P]),
     "ts_set_chaining": (_I, [_P, _I]),
     "ts_flush": (_I, [_P]),
     "ts_kernel_launches": (_I64, [_P]),
@@ -191,16 +191,17 @@ class PlanPass(ctypes.Structure):
                 ("rot_after", ctypes.c_uint64), ("dup", ctypes.c_int)]
 
 
-def ts_plan(N, prec=TS_C64, tile_bits=0, coalesce_bits=0, order=4, nsteps=1):
-    """The fused-pass plan (host only, no GPU): a list of group dicts and a list of pass dicts."""
+def ts_plan(N, prec=TS_C64, tile_bits=0, coalesce_bits=0, order=4, nsteps=1, chain=0):
+    """The fused-pass plan (host only, no GPU): a list of group dicts and a list of pass dicts.
+    chain: bit 1 = the call continues a held-back pass, bit 2 = it holds back its final pass."""
     ng, npass = ctypes.c_int(), ctypes.c_int64()
-    st = _lib.ts_plan(int(N), int(prec), int(tile_bits), int(coalesce_bits), int(order), int(nsteps),
+    st = _lib.ts_plan(int(N), int(prec), int(tile_bits), int(coalesce_bits), int(order), int(nsteps), int(chain),
                       None, 0, ctypes.byref(ng), None, 0, ctypes.byref(npass))
     if st:
         raise TS4Error(st, "ts_plan: invalid arguments")
     G = (PlanGroup * max(ng.value, 1))()
     P = (PlanPass * max(npass.value, 1))()
-    _check(_lib.ts_plan(int(N), int(prec), int(tile_bits), int(coalesce_bits), int(order), int(nsteps),
+    _check(_lib.ts_plan(int(N), int(prec), int(tile_bits), int(coalesce_bits), int(order), int(nsteps), int(chain),
                         ctypes.cast(G, _P), ng.value, ctypes.byref(ng), ctypes.cast(P, _P), npass.value,
                         ctypes.byref(npass)), None)
     groups = [dict(c=g.c, w=g.w, h=g.h) for g in G[:ng.value]]

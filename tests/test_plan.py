@@ -26,11 +26,14 @@ def _mask(lo, n):
     return ((1 << n) - 1) << lo
 
 
-def replay(groups, passes, layers):
+def replay(groups, passes, layers, state=None, slot_base=0, complete=True):
+    """Replays one call's passes; state carries (layers done per group, last slot) across
+    chained calls, whose slot k is global slot slot_base + k."""
     g = len(groups)
     gmask = [_mask(gr["w"], gr["h"]) for gr in groups]
-    done = [0] * g           # layers finished per group
-    last_slot = -1
+    if state is None:
+        state = {"done": [0] * g, "last_slot": -1}
+    done = state["done"]     # layers finished per group
     for p in passes:
         gi = p["group"]
         assert p["dup"] == 0
@@ -41,17 +44,19 @@ def replay(groups, passes, layers):
                 continue
             if side == "rot_after":
                 # the slot sits between the two sides
-                k = p["slot"]
-                assert k == last_slot + 1, (k, last_slot)
+                k = slot_base + p["slot"]
+                assert k == state["last_slot"] + 1, (k, state["last_slot"])
                 assert all(d == k for d in done), (k, done)
-                last_slot = k
+                state["last_slot"] = k
             if m == 0:
                 continue
             assert m == gmask[gi], (side, hex(m), hex(gmask[gi]))
-            assert last_slot == done[gi], "rotation before the slot of its layer"
+            assert state["last_slot"] == done[gi], "rotation before the slot of its layer"
             done[gi] += 1
-    assert done == [layers] * g
-    assert last_slot == layers
+    if complete:
+        assert done == [slot_base + layers] * g
+        assert state["last_slot"] == slot_base + layers
+    return state
 
 
 @pytest.mark.parametrize("N,tb,cb", [(12, 12, 3), (14, 12, 2), (17, 12, 3), (20, 12, 3), (23, 12, 2),
@@ -116,3 +121,31 @@ def test_plan_rejects_bad_arguments(ts4):
                  (20, ts4.TS_C64, 12, 3, 4, 0)]:    # no steps
         with pytest.raises(ts4.TS4Error):
             ts4.ts_plan(*args)
+
+
+@pytest.mark.parametrize("N,tb,cb", [(17, 12, 3), (23, 12, 2), (28, 12, 3), (33, 12, 3)])
+@pytest.mark.parametrize("order", [4, 2])
+def test_chained_calls_replay_as_one_run(ts4, N, tb, cb, order):
+    """Calls with chaining (ts_set_chaining): the first holds back its final pass, the middle
+    ones continue and hold back, the last continues and completes.  Replayed in sequence
+    with global slot numbers, they must form the full decomposition of all their layers."""
+    steps = [1, 2, 1]
+    chains = [2, 3, 1]
+    state, base, groups = None, 0, None
+    for n, ch in zip(steps, chains):
+        groups, passes = ts4.ts_plan(N, ts4.TS_C64, tb, cb, order, n, chain=ch)
+        layers = LAYERS_PER_STEP[order] * n
+        last = ch == 1
+        state = replay(groups, passes, layers, state, slot_base=base, complete=last)
+        if not last:
+            # exactly the final pass is missing: one group one layer short, its last slot pending
+            short = [i for i, d in enumerate(state["done"]) if d == base + layers - 1]
+            assert len(short) == 1 and short[0] == (1 if len(groups) >= 3 else 0)
+            assert state["last_slot"] == base + layers - 1
+        base += layers
+    assert state["done"] == [base] * len(groups)
+
+
+def test_chaining_needs_two_groups(ts4):
+    with pytest.raises(ts4.TS4Error):
+        ts4.ts_plan(12, ts4.TS_C64, 12, 3, 4, 1, chain=2)
