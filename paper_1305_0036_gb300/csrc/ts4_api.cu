@@ -540,6 +540,33 @@ std::vector<Group> make_groups(int N, int TB, int cbits)
     return g;
 }
 
+// Default coalescing width for N spins and TB-bit tiles: the precision's default (64-byte
+// runs), or one bit less (32-byte runs, still whole sectors) when that saves a bit group,
+// i.e. one pass per layer.
+int default_cbits_for(ts_prec p, int N, int TB)
+{
+    const int cb = default_cbits(p);
+    if (N <= TB || cb - 1 < 2)
+        return cb;
+    return make_groups(N, TB, cb - 1).size() < make_groups(N, TB, cb).size() ? cb - 1 : cb;
+}
+
+// The same for an ensemble: the width that minimises the amplitude-passes of all its states
+// (ties keep the precision's default).
+int default_cbits_batch(ts_prec p, int TB, const std::vector<int> &N, const std::vector<int> &nstates)
+{
+    const int cb0 = default_cbits(p);
+    auto cost = [&](int cb) {
+        double c = 0.0;
+        for (size_t s = 0; s < N.size(); s++) {
+            const int g = N[s] <= TB ? 1 : (int)make_groups(N[s], TB, cb).size();
+            c += (double)nstates[s] * std::ldexp(1.0, N[s]) * (g > 1 ? g - 1 : 1);
+        }
+        return c;
+    };
+    return (cb0 - 1 >= 2 && cost(cb0 - 1) < cost(cb0)) ? cb0 - 1 : cb0;
+}
+
 struct ChunkInfo {
     int n;
     int lo[8], hi[8];
@@ -1238,7 +1265,7 @@ ts_status ts_plan(int N, ts_prec prec, int tile_bits, int coalesce_bits, int ord
         return TS_ERR_ARG;
     const int TB = tile_bits ? tile_bits : default_tile(prec);
     const int RB = reg_bits(prec);
-    const int cb = coalesce_bits ? coalesce_bits : default_cbits(prec);
+    const int cb = coalesce_bits ? coalesce_bits : default_cbits_for(prec, N, TB);
     if (!tile_supported(prec, TB) || N < TB || cb < 1 || cb > TB - RB)
         return TS_ERR_ARG;
     const std::vector<Group> G = make_groups(N, TB, cb);
@@ -1320,7 +1347,7 @@ ts_status ts_create(ts_ctx **out, int N, const double *Jx, const double *Jy, con
         }
     ctx->RB = reg_bits(prec);
     ctx->TB = default_tile(prec);
-    ctx->cbits = default_cbits(prec);
+    ctx->cbits = default_cbits_for(prec, N, ctx->TB);
     ts_status st = TS_OK;
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess)
@@ -1690,7 +1717,7 @@ ts_status ts_set_schedule(ts_ctx *ctx, int kernel, int tile_bits, int coalesce_b
     if (kernel != TS_KERNEL_FUSED && kernel != TS_KERNEL_BASIC)
         return fail(ctx, TS_ERR_ARG, "ts_set_schedule: unknown kernel");
     const int tb = tile_bits ? tile_bits : default_tile(ctx->prec);
-    const int cb = coalesce_bits ? coalesce_bits : default_cbits(ctx->prec);
+    const int cb = coalesce_bits ? coalesce_bits : default_cbits_for(ctx->prec, ctx->N, tb);
     if (!tile_supported(ctx->prec, tb))
         return fail(ctx, TS_ERR_ARG, "ts_set_schedule: tile size not provided for this precision");
     if (cb < 1 || cb > tb - ctx->RB)
@@ -2008,6 +2035,10 @@ ts_status ts_batch_create(ts_batch **out, int nsys, const int *N, const double *
         }
         b->TB = tb;
     }
+    {
+        std::vector<int> ns(N, N + nsys), ks(nstates, nstates + nsys);
+        b->cbits = default_cbits_batch(prec, b->TB, ns, ks);
+    }
     TS_BCUDA(b, cudaMallocHost(&b->hout, (kMaxN + 8) * sizeof(double)));
     TS_BCUDA(b, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
     *out = b;
@@ -2073,7 +2104,12 @@ ts_status ts_batch_set_schedule(ts_batch *b, int tile_bits, int coalesce_bits)
     for (auto *c : b->sys)
         nmin = std::min(nmin, c->N);
     const int tb = tile_bits ? tile_bits : std::min(default_tile(b->prec), nmin);
-    const int cb = coalesce_bits ? coalesce_bits : default_cbits(b->prec);
+    std::vector<int> ns, ks;
+    for (int s = 0; s < b->nsys; s++) {
+        ns.push_back(b->sys[(size_t)s]->N);
+        ks.push_back(b->nstates[(size_t)s]);
+    }
+    const int cb = coalesce_bits ? coalesce_bits : default_cbits_batch(b->prec, tb, ns, ks);
     if (!tile_supported(b->prec, tb) || tb > nmin || cb < 1 || cb > tb - reg_bits(b->prec))
         return bfail(b, TS_ERR_ARG, "ts_batch_set_schedule: tile not provided or larger than the smallest system");
     b->TB = tb;
