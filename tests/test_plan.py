@@ -149,3 +149,15 @@ def test_chained_calls_replay_as_one_run(ts4, N, tb, cb, order):
 def test_chaining_needs_two_groups(ts4):
     with pytest.raises(ts4.TS4Error):
         ts4.ts_plan(12, ts4.TS_C64, 12, 3, 4, 1, chain=2)
+
+
+def test_default_coalescing_width(ts4):
+    """Defaults: 3 coalescing spins for complex64, one fewer where that saves a bit group."""
+    def widths(N):
+        groups, _ = ts4.ts_plan(N, ts4.TS_C64, 12, 0, 4, 1)
+        return [12 - gr["h"] for gr in groups[1:]]
+    assert widths(22) == [2]                 # 2 spins: one window of 10 instead of two
+    assert widths(28) == [4, 4]              # 2 windows either way: keep 3 (windows of 8)
+    assert widths(20) == [4]                 # one window of 8 with 3 spins already
+    groups, _ = ts4.ts_plan(23, ts4.TS_C128, 12, 0, 4, 1)
+    assert len(groups) == 3                  # complex128 never goes below 2 spins
