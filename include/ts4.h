@@ -196,7 +196,10 @@ TS4_API const char *ts_last_error(const ts_ctx *ctx);
  *   kernel          TS_KERNEL_FUSED or TS_KERNEL_BASIC
  *   tile_bits       log2 of the amplitudes one thread block holds (0 = default)
  *   coalesce_bits   the s lowest spins every block keeps, so that each block
- *                   touches runs of 2^s consecutive amplitudes (0 = default)
+ *                   touches runs of 2^s consecutive amplitudes (0 = default: 3 for
+ *                   complex64 and 2 for complex128, 64-byte runs, or 2 for complex64
+ *                   when that needs one bit group fewer at this N)
+ * Runs a pass held back by chaining first (ts_set_chaining).
  * Errors: TS_ERR_ARG for a shape this build does not provide.
  */
 TS4_API ts_status ts_set_schedule(ts_ctx *ctx, int kernel, int tile_bits, int coalesce_bits);
@@ -337,7 +340,8 @@ TS4_API ts_status ts_batch_set_states(ts_batch *b, int sys, const void *amps, in
 /* Copies the states of system sys out (host memory if on_device == 0). */
 TS4_API ts_status ts_batch_get_states(ts_batch *b, int sys, void *amps, int on_device);
 
-/* Tile bits and coalescing bits for every system (0 = default); the tile may not exceed the smallest N. */
+/* Tile bits and coalescing bits for every system (0 = default; the default width is the one
+ * that minimises the ensemble's amplitude-passes); the tile may not exceed the smallest N. */
 TS4_API ts_status ts_batch_set_schedule(ts_batch *b, int tile_bits, int coalesce_bits);
 
 /* The ensemble's tile bits and coalescing bits (either pointer may be NULL). */
