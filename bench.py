@@ -152,41 +152,64 @@ def max_over_ranks(ws, v):
 
 # ---------------------------------------------------------------- CPU oracle baseline
 
-def oracle_sample(nsteps=1):
-    """Times the oracle on a bounded sample and scales it to the N=28 step.
+# The oracle's U4 step (Sec. 2: U4 = five U2's, each U2 = U1(t/2) then U1^dag(-t/2), each U1 three
+# parts; a z part is one Z-like phase, an x or y part is a global rotation, a phase, the inverse
+# rotation and an exact 2^-N scale) is, operation by operation:
+ORACLE_U4_PHASES, ORACLE_U4_ROTATIONS, ORACLE_U4_SCALES = 30, 40, 20
 
-    The oracle's U4 step is 40 global rotations (N 2^{N-1} pair updates each) and
-    30 diagonal phases (2^N states x (N(N-1)/2 + N) terms each).  Both are timed at
-    N=20 on the same dipolar chain; the N=28 step time is their sum scaled by the
-    exact operation-count ratios.
+
+class OracleSample:
+    """Times the FP64 CPU oracle, as it stands, on the benchmark's own N=28 state, in place.
+
+    The three kinds of operation of its U4 step are timed at full size: a Z-like phase
+    (O(N^2) bond terms per amplitude), a global rotation (N spins x 2^(N-1) pair updates) and
+    the exact 2^-N scale.  The U4 step time is 30 phases + 40 rotations + 20 scales, the exact
+    operation count of the oracle's U4.
     """
-    import numpy as np
-    import oracle
-    from paper_1305_0036_gb300 import workloads as W
-    n = 20
-    s = W.dipolar_chain(n)
-    H = oracle.Hamiltonian(n, s.Jx, s.Jy, s.Jz, hz=s.hz)
-    psi = W.random_phase_state(n, 1)
-    t0 = time.perf_counter()
-    for _ in range(nsteps):
-        psi = oracle.ts4(psi, H, TAU, 1)
-    t_step20 = (time.perf_counter() - t0) / nsteps
-    t0 = time.perf_counter()
-    oracle.rotate_all(psi, n, oracle.X)
-    t_rot = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.phase(psi, n, s.Jz, s.hz, TAU)
-    t_ph = time.perf_counter() - t0
-    N = 28
-    rot_scale = (N * 2 ** (N - 1)) / (n * 2 ** (n - 1))
-    ph_scale = (2 ** N * (N * (N - 1) / 2 + N)) / (2 ** n * (n * (n - 1) / 2 + n))
-    model20 = 40 * t_rot + 30 * t_ph
-    # the remainder of the measured N=20 step (scales, copies) scales like the rotations
-    rest = max(t_step20 - model20, 0.0)
-    t28 = 40 * t_rot * rot_scale + 30 * t_ph * ph_scale + rest * rot_scale
-    return {"t_step_n20_s": t_step20, "t_step_n28_s": t28, "cores": oracle.num_threads(),
-            "sample": f"{nsteps} oracle U4 step(s) of the N=20 dipolar chain ({t_step20:.2f} s/step) plus one "
-                      "rotation layer and one phase at N=20, scaled to N=28 by the oracle's operation counts"}
+
+    def __init__(self, N=28):
+        import numpy as np
+        import oracle
+        from paper_1305_0036_gb300 import workloads as W
+        self.np, self.oracle, self.N = np, oracle, N
+        self.lib = oracle.lib()
+        s = W.dipolar_chain(N)
+        self.J = np.ascontiguousarray(s.Jz)
+        self.h = np.ascontiguousarray(s.hz)
+        self.psi = W.random_phase_state(N, W.SEED_BASE + 3)   # complex128, 2^N amplitudes
+        self.cores = oracle.num_threads()
+
+    def phase(self):
+        t0 = time.perf_counter()
+        self.lib.oracle_phase(self.psi.ctypes.data, self.N, self.J.ctypes.data, self.h.ctypes.data, TAU)
+        return time.perf_counter() - t0
+
+    def rotation_and_scale(self):
+        t0 = time.perf_counter()
+        self.lib.oracle_rotate_all(self.psi.ctypes.data, self.N, self.oracle.X)
+        t1 = time.perf_counter()
+        self.lib.oracle_scale(self.psi.ctypes.data, self.N, 2.0 ** (-self.N / 2))
+        return t1 - t0, time.perf_counter() - t1
+
+    @staticmethod
+    def u4_seconds(t_phase, t_rot, t_scale):
+        return ORACLE_U4_PHASES * t_phase + ORACLE_U4_ROTATIONS * t_rot + ORACLE_U4_SCALES * t_scale
+
+    def u1_measured(self):
+        """One real oracle U1 on the same state (for checking the composition: U1 = 3 phases +
+        4 rotations + 2 scales)."""
+        import oracle
+        from paper_1305_0036_gb300 import workloads as W
+        s = W.dipolar_chain(self.N)
+        H = oracle.Hamiltonian(self.N, s.Jx, s.Jy, s.Jz, hz=s.hz)
+        t0 = time.perf_counter()
+        self.lib.oracle_apply(self.psi.ctypes.data, self.N, *H.args(), 1, TAU)
+        return time.perf_counter() - t0
+
+
+SAMPLE_TEXT = ("the FP64 oracle at N=28 on the benchmark's own dipolar chain and state (complex128, 4 GiB, "
+               "in place): {what}; TS4 step = 30 Z-like phases + 40 global rotations + 20 exact scales "
+               "(the operation count of the oracle's U4)")
 
 
 def run_reference(args, ws, rank):
@@ -194,29 +217,148 @@ def run_reference(args, ws, rank):
         return
     import oracle
     oracle.build()
+    smp = OracleSample(28)
+    # the phase (about a minute of one core's work per 2^24 amplitudes) is timed once, in the
+    # first warm-up step; every step times a global rotation and a scale
+    t_phase = smp.phase()
     for _ in range(args.warmup):
-        oracle_sample(1)
+        smp.rotation_and_scale()
+    rots, scs, walls = [], [], []
     t0 = time.perf_counter()
-    t28 = []
-    info = None
     for _ in range(args.steps):
-        info = oracle_sample(1)
-        t28.append(info["t_step_n28_s"])
+        w0 = time.perf_counter()
+        r, c = smp.rotation_and_scale()
+        walls.append(time.perf_counter() - w0)
+        rots.append(r)
+        scs.append(c)
     wall = time.perf_counter() - t0
-    ms = 1000 * statistics.mean(t28)
-    v = 1000.0 / ms
+    t_u4 = OracleSample.u4_seconds(t_phase, statistics.mean(rots), statistics.mean(scs))
+    v = 1.0 / t_u4
+    sample = SAMPLE_TEXT.format(what=f"each step times one global rotation and one scale "
+                                     f"({1000 * statistics.mean(rots):.0f} + {1000 * statistics.mean(scs):.0f} ms), "
+                                     f"the phase was timed once before them ({t_phase:.2f} s)")
     line = {"metric": METRIC, "value": v, "unit": "TS4 steps/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(walls), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "N": 28, "prec": "c128 (oracle, FP64 CPU)"},
-            "cpu_baseline": {"value": v, "unit": "TS4 steps/s", "cores": info["cores"], "kind": "oracle",
-                             "sample": info["sample"]},
+            "ms_per_step_is": "wall time of one timed sample (one global rotation + one scale at N=28)",
+            "ts4_step_s": t_u4,
+            "parts_s": {"phase": t_phase, "rotation": statistics.mean(rots), "scale": statistics.mean(scs)},
+            "cpu_baseline": {"value": v, "unit": "TS4 steps/s", "cores": smp.cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": v, "unit": "TS4 steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------- GPU arm
+
+def accuracy_vs_c128(ts4, torch, ctx64, ctx128):
+    """complex64 against complex128 after the same steps from the same state (Sec. 4.2's
+    accuracy figures): state difference, norm drift, largest S^z difference."""
+    a = ctx64.psi.to(torch.complex128)
+    d = a - ctx128.psi
+    l2 = float(torch.linalg.vector_norm(d).item())
+    mx = float(d.abs().max().item())
+    del a, d
+    n64, n128 = ctx64.norm(), ctx128.norm()
+    dsz = float(abs(ctx64.sz() - ctx128.sz()).max())
+    return {"l2": l2, "max_abs": mx, "norm_drift_c64": abs(n64 - 1.0), "norm_drift_c128": abs(n128 - 1.0),
+            "max_abs_dSz": dsz}
+
+
+def oracle_cross_check(ts4):
+    """The benchmark's schedules against the FP64 oracle where it runs in seconds: the N=23
+    dipolar chain with the tile shapes of both arms (12-bit tiles; 3 coalescing spins for
+    complex64, 2 for complex128), which give 3 bit groups and the slot-less middle pass as at
+    N=28; 2 TS4 steps of tau = 0.01 from the random-phase state."""
+    import numpy as np
+    import oracle
+    from paper_1305_0036_gb300 import workloads as W
+    N, n = 23, 2
+    s = W.dipolar_chain(N)
+    psi0 = W.random_phase_state(N, W.SEED_BASE + 3)
+    ref = oracle.ts4(psi0, oracle.Hamiltonian(N, s.Jx, s.Jy, s.Jz, hz=s.hz), TAU, n)
+    out = {"N": N, "steps": n, "workload": "dipolar XXZ chain, random-phase state"}
+    for prec, tile, cb in (("c64", 12, 3), ("c128", 12, 2)):
+        c = ts4.Context.from_system(s, prec=prec)
+        c.set_schedule(ts4.TS_KERNEL_FUSED, tile, cb)
+        c.set_state(psi0)
+        c.step(TAU, n)
+        sch = c.schedule()
+        d = c.get_state().astype(np.complex128) - ref
+        c.close()
+        out[prec] = {"max_abs": float(np.abs(d).max()), "l2": float(np.linalg.norm(d)),
+                     "tile_bits": sch["tile_bits"], "coalesce_bits": sch["coalesce_bits"], "groups": sch["groups"]}
+    return out
+
+
+def config4_ensemble(ts4, torch, dev, steps):
+    """Config 4: 256 Haar states, 64 each at N = 16, 18, 20, 22 (XYZ chains 1.0/0.8/0.5, fields
+    uniform in [-1, 1]), tau = 0.02, complex64, autotuned tile; ms per ensemble step over one
+    ts_batch_step(tau, steps) graph launch."""
+    from paper_1305_0036_gb300 import workloads as W
+    cfg = W.config(3)
+    systems, k = cfg["systems"], cfg["states_per_system"]
+    b = ts4.Batch(systems, [k] * len(systems), prec="c64", device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(cfg["state_seed"])
+    for i, s in enumerate(systems):
+        z = torch.randn((k, 1 << s.N), dtype=torch.complex64, device=dev, generator=g)
+        z /= torch.linalg.vector_norm(z, dim=1, keepdim=True)
+        b.set_states(i, z)
+        del z
+    tune_ms = b.autotune(cfg["tau"], reps=2)
+    sch = b.schedule()
+    b.step(cfg["tau"], 2)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(cfg["tau"], steps)
+    e1.record(b.stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    norms = b.norms()
+    amps = sum(k << s.N for s in systems)
+    out = {"workload": "256 Haar states, 64 each at N=16/18/20/22, XYZ chains (1.0, 0.8, 0.5), h~U[-1,1], "
+                       "tau=0.02, complex64", "ms_per_ensemble_step": ms, "steps_timed": steps,
+           "timed_call": f"one ts_batch_step(tau, {steps}) (one CUDA graph launch)",
+           "effective_gbs": 40 * 8 * amps / (ms / 1000.0) / 1e9, "tile_bits": sch["tile_bits"],
+           "coalesce_bits": sch["coalesce_bits"], "autotune_best_ms": tune_ms,
+           "max_norm_drift": float(abs(norms - 1.0).max())}
+    b.close()
+    return out
+
+
+def config5_capacity(ts4, torch, dev, steps):
+    """Config 5: N=33 XYZ chain (1.0, 0.8, 0.5), h=0.1, Neel state, tau=0.02, complex64 (64 GiB
+    state in place); ms per TS4 step over one ts_step(tau, steps) call."""
+    from paper_1305_0036_gb300 import workloads as W
+    cfg = W.config(4)
+    s = cfg["system"]
+    N = s.N
+    ctx = ts4.Context.from_system(s, prec="c64", device=dev)
+    ctx.set_basis_state(cfg["state"][1])
+    ctx.step(cfg["tau"], 1)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    ctx.step(cfg["tau"], steps)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    sch = ctx.schedule()
+    norm = ctx.norm()
+    state_bytes = 8 << N
+    out = {"workload": "N=33 open XYZ chain (1.0, 0.8, 0.5), h=0.1, Neel state, tau=0.02, complex64",
+           "ms_per_step": ms, "steps_timed": steps, "state_gib": state_bytes / 2 ** 30,
+           "groups": sch["groups"], "passes_per_step": sch["passes_per_step"],
+           "effective_gbs": 40 * state_bytes / (ms / 1000.0) / 1e9,
+           "pass_traffic_gbs": sch["passes_per_step"] * 2 * state_bytes / (ms / 1000.0) / 1e9,
+           "norm_drift": abs(norm - 1.0)}
+    ctx.close()
+    return out
+
 
 def run_ours(args, ws, rank, local):
     import numpy as np
@@ -308,6 +450,7 @@ def run_ours(args, ws, rank, local):
     e2e_value = ws * args.steps / e2e_s
     e2e_upload_ms = 1000.0 * (t_up - t0)
     e2e_step_ms = 1000.0 * (t1 - t_up) / args.steps
+    ctx.flush()          # the state after K steps from psi_0, for the accuracy figures below
 
     line = {
         "metric": METRIC, "value": value, "unit": "TS4 steps/s", "n_gpus": ws, "steps": args.steps,
@@ -333,20 +476,19 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": launches,
         "clocks": clk,
     }
-    ctx.close()
 
     if args.compare_c128 and prec == "c64":
+        # the complex128 arm: the same K steps from the same state (the complex64 initial state
+        # converted exactly), one ts_step(tau, K) call timed with events
         c = ts4.Context.from_system(s, prec="c128", device=dev)
         c.set_state(np.asarray(host.numpy(), dtype=np.complex128))
-        c.step(TAU, 1)
         torch.cuda.synchronize(dev)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        k = 2
         a.record(c.stream)
-        c.step(TAU, k)
+        c.step(TAU, args.steps)
         b.record(c.stream)
         torch.cuda.synchronize(dev)
-        ms128 = a.elapsed_time(b) / k
+        ms128 = a.elapsed_time(b) / args.steps
         # complex128 is bound by the FP64 pipes, not by HBM: per amplitude and step the 20 layers
         # take N butterfly stages of 2 FP64 adds each, and the 21 slots 3 complex multiplies of
         # 4 FP64 instructions each (FMA counted once).  Peak: the nominal 1.25 TFLOP/s of FP64
@@ -354,23 +496,44 @@ def run_ours(args, ws, rank, local):
         fp64_inst = float(2 ** N) * (20 * N * 2 + 21 * 12)
         fp64_rate = fp64_inst / (ms128 / 1000.0) / 1e12
         line["c128"] = {"value": 1000.0 / ms128, "unit": "TS4 steps/s", "ms_per_step": ms128,
+                        "steps_timed": args.steps, "speedup_of_c64": (1000.0 / ms_step) / (1000.0 / ms128),
                         "effective_gbs": 40 * (16 << N) / (ms128 / 1000.0) / 1e9,
                         "roofline": {"bound": "alu", "achieved": fp64_rate, "peak": 0.625,
                                      "unit": "T FP64 instructions/s", "frac": fp64_rate / 0.625,
                                      "peak_kind": "nominal FP64 rate (1.25 TFLOP/s)"}}
+        # accuracy of the benchmarked complex64 run (its end-to-end leg: K chained one-step calls
+        # from psi_0) against the complex128 run; targets 1e-5 for S^z and the norm drift
+        err = accuracy_vs_c128(ts4, torch, ctx, c)
+        err.update({"vs": f"complex128 GPU run (parity with the FP64 oracle: 1e-12), same state, same {args.steps} steps",
+                    "steps": args.steps, "targets": {"max_abs_dSz": 1e-5, "norm_drift_c64": 1e-5}})
+        line["err"] = err
         c.close()
+    ctx.close()
+    del host
+    torch.cuda.empty_cache()
+
+    if rank == 0 and ws == 1 and not args.no_oracle_check:
+        line["err_vs_oracle"] = oracle_cross_check(ts4)
+    if not args.no_configs and N == 28:
+        line["config4"] = config4_ensemble(ts4, torch, dev, 20)
+        torch.cuda.empty_cache()
+        line["config5"] = config5_capacity(ts4, torch, dev, 2)
+        torch.cuda.empty_cache()
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        import oracle
-        info = oracle_sample(4)
-        # the same sample on one core (one U4 step at N=20 instead of four)
-        oracle.set_num_threads(1)
-        one = oracle_sample(1)
-        oracle.set_num_threads(info["cores"])
-        line["cpu_baseline"] = {"value": 1.0 / info["t_step_n28_s"], "unit": "TS4 steps/s",
-                                "cores": info["cores"], "kind": "oracle", "sample": info["sample"],
-                                "single_thread": {"value": 1.0 / one["t_step_n28_s"], "cores": one["cores"],
-                                                  "sample": one["sample"]}}
+        smp = OracleSample(28)
+        t_ph = smp.phase()
+        t_rot, t_sc = smp.rotation_and_scale()
+        t_u4 = OracleSample.u4_seconds(t_ph, t_rot, t_sc)
+        line["cpu_baseline"] = {"value": 1.0 / t_u4, "unit": "TS4 steps/s", "cores": smp.cores, "kind": "oracle",
+                                "sample": SAMPLE_TEXT.format(what=f"one phase ({t_ph:.2f} s), one global rotation "
+                                                                  f"({t_rot:.2f} s) and one scale ({t_sc:.3f} s) timed"),
+                                "ts4_step_s": t_u4}
+        if args.validate_cpu_model:
+            t_u1 = smp.u1_measured()
+            model = 3 * t_ph + 4 * t_rot + 2 * t_sc
+            line["cpu_baseline"]["u1_check"] = {"measured_s": t_u1, "composed_s": model,
+                                                "residual": t_u1 / model - 1.0}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -387,6 +550,10 @@ def main():
     ap.add_argument("--compare-c128", action="store_true", default=True)
     ap.add_argument("--no-compare-c128", dest="compare_c128", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the config-4 and config-5 lines")
+    ap.add_argument("--validate-cpu-model", action="store_true",
+                    help="also time one real oracle U1 at N=28 against its composition from the parts")
     ap.add_argument("--spins", type=int, default=28,
                     help="chain length N (28 is the benchmark; smaller N only for profiling captures)")
     args = ap.parse_args()

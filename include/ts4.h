@@ -174,8 +174,11 @@ TS4_API ts_status ts_set_chaining(ts_ctx *ctx, int enable);
 TS4_API ts_status ts_flush(ts_ctx *ctx);
 
 /*
- * Evaluates an observable (TS_NORM, TS_ENERGY, TS_SZ, TS_ECHO, TS_OVERLAP)
- * into host memory `out` (sizes above).  Sums are accumulated in FP64.
+ * Evaluates an observable (TS_NORM, TS_ENERGY, TS_SZ, TS_ECHO, TS_OVERLAP, ...)
+ * into host memory `out` (sizes above).  Sums are accumulated in FP64; for
+ * complex64 norms and <S^z> each thread first sums exact squares of the FP32
+ * components in double-float (pairs of floats), whose error is of order
+ * 1e-11 relative, then the threads' sums are added in FP64.
  * Synchronises the context's stream.  TS_ECHO/TS_OVERLAP without a saved
  * reference return TS_ERR_STATE.
  */
@@ -187,7 +190,7 @@ TS4_API ts_status ts_get_state(ts_ctx *ctx, void *amps, int on_device);
 /* Frees everything the library allocated.  NULL is accepted. */
 TS4_API ts_status ts_destroy(ts_ctx *ctx);
 
-/* Text of the last error of ctx (never NULL; "" if none).  ctx may be NULL. */
+/* Text of the last error or warning of ctx (never NULL; "" if none).  ctx may be NULL. */
 TS4_API const char *ts_last_error(const ts_ctx *ctx);
 
 /*
@@ -215,9 +218,20 @@ TS4_API ts_status ts_get_schedule(const ts_ctx *ctx, int *kernel, int *tile_bits
 /*
  * The time-step bound of Eq. 4: returns
  *   [ max_{j,k} ( sum_a (h^a_j/2)^2 + sum_a (J^a_jk/4)^2 )^{1/2} ]^{-1}
- * for the context's Hamiltonian; steps should satisfy |tau| << this value.
+ * for the context's Hamiltonian (infinity when H = 0); steps should satisfy
+ * |tau| << this value.  ts_step and ts_step_order accept larger steps but record a
+ * warning in ts_last_error (text starting "warning: ") when |tau| is at least
+ * this bound; they still return TS_OK.
  */
 TS4_API double ts_step_bound(const ts_ctx *ctx);
+
+/*
+ * The same bound from the couplings directly, on the host only (no device, no
+ * context): Jx, Jy, Jz are N*N row-major (upper triangle read), hx, hy, hz length
+ * N or NULL.  Returns -1 for N outside [1, 34] or a NULL coupling matrix.
+ */
+TS4_API double ts_step_bound_host(int N, const double *Jx, const double *Jy, const double *Jz, const double *hx,
+                                  const double *hy, const double *hz);
 
 /*
  * Global basis index of local amplitude e of thread block f for a tile made of
@@ -268,10 +282,12 @@ TS4_API ts_status ts_plan(int N, ts_prec prec, int tile_bits, int coalesce_bits,
  * The paper's phase-table mode (Sec. 3.1: the energies of every basis state are
  * precomputed once and each phase reads them), kept for an A/B comparison with
  * the bit-test slots.  enable != 0 builds three tables E_x, E_y, E_z of 2^N
- * floats each (12 bytes per basis state; N = 28: 3 GiB) on the device; the basic
- * kernel (TS_KERNEL_BASIC) then reads its slot angles from them.  The fused
- * kernel forms its angles from the bits and ignores the tables.  enable = 0
- * frees them.  The tables follow later ts_set_transverse_fields calls.
+ * entries each on the device: doubles for complex128 (24 bytes per basis state,
+ * as in the paper; N = 28: 6 GiB), floats for complex64 (12 bytes per basis
+ * state; N = 28: 3 GiB).  The basic kernel (TS_KERNEL_BASIC) then reads its slot
+ * angles from them.  The fused kernel forms its angles from the bits and ignores
+ * the tables.  enable = 0 frees them.  The tables follow later
+ * ts_set_transverse_fields calls.
  * Errors: TS_ERR_OOM if the tables do not fit, TS_ERR_CUDA.
  */
 TS4_API ts_status ts_set_phase_tables(ts_ctx *ctx, int enable);
@@ -293,14 +309,15 @@ TS4_API ts_status ts_autotune(ts_ctx *ctx, double tau, int reps, const char *cac
 /*
  * Norm and <S^z_j> of a caller-owned device state, computed without allocating
  * any device memory.  The paper has no counterpart: this entry point serves
- * callers that cannot call cudaMalloc where they need these numbers -- code
- * running while a stream is captured into a CUDA graph (allocation is not a
- * capturable operation) and hosts whose device memory is owned by their own
- * allocator.
- *   psi_dev  2^N amplitudes of precision prec, device memory (read only).
+ * callers that cannot call cudaMalloc where they need these numbers -- hosts
+ * whose device memory is owned by their own pool allocator, plug-ins that must
+ * not grow the device footprint, loops that must not allocate once started.
+ *   psi_dev  2^N amplitudes of precision prec, device memory (read only).  A
+ *            state buffer bound to a context with chaining on (ts_set_chaining)
+ *            lacks the held-back final pass: call ts_flush on that context first.
  *   out_dev  N + 1 doubles of device memory owned by the caller:
  *            out[0] = sum_s |psi_s|^2, out[1 + j] = sum_s |psi_s|^2 (bit_j(s) - 1/2)
- *            = <S^z_{j+1}>.
+ *            = <S^z_{j+1}>; sums accumulated as in ts_observe.
  *   cuda_stream  stream to enqueue on (NULL = legacy default stream); no host
  *            synchronisation.
  * Scratch: a static device array of 1024 x 35 doubles (about 280 KB), held by

@@ -66,6 +66,7 @@ def lib():
                 "oracle_overlap": (None, [P, P, i, P]),
                 "oracle_apply_hamiltonian": (None, [P, P, i, P, P, P, P, P, P]),
                 "oracle_energy": (d, [P, i, P, P, P, P, P, P]),
+                "oracle_correlations": (None, [P, i, P, P, P, P, P]),
                 "oracle_num_threads": (i, []),
                 "oracle_set_num_threads": (None, [i]),
             }
@@ -196,6 +197,17 @@ def apply_hamiltonian(psi, H: Hamiltonian):
 
 def energy(psi, H: Hamiltonian):
     return float(lib().oracle_energy(_ptr(_state(psi, H.N)), H.N, *H.args()))
+
+
+def correlations(psi, N):
+    """Two-spin correlations <S^a_i S^a_j> (a = "z", "x", "y": N x N arrays, diagonal =
+    norm/4) and the transverse magnetisations <S^x_j>, <S^y_j>, by direct action of the spin
+    operators: returns (C, mx, my) with C a dict of the three matrices."""
+    a = _state(psi, N)
+    czz, cxx, cyy = np.zeros((N, N)), np.zeros((N, N)), np.zeros((N, N))
+    mx, my = np.zeros(N), np.zeros(N)
+    lib().oracle_correlations(_ptr(a), N, _ptr(czz), _ptr(cxx), _ptr(cyy), _ptr(mx), _ptr(my))
+    return {"z": czz, "x": cxx, "y": cyy}, mx, my
 
 
 def num_threads() -> int:

@@ -35,7 +35,8 @@
  *   oracle_u2           U2(t) = U1^dag(-t/2) U1(t/2)                 (Sec. 2)
  *   oracle_u4           U4(t) = U2(at)U2(at)U2((1-4a)t)U2(at)U2(at) (Sec. 2)
  * and the observables of Sec. 4.2 by their definitions (norm, <S^z_i>, <H>
- * by direct application of the Pauli operators, overlap for the echo Eq. 11).
+ * by direct application of the Pauli operators, overlap for the echo Eq. 11,
+ * two-spin correlations and transverse magnetisations).
  *
  * Amplitudes are C99 double complex, 2^N of them, in basis-index order.
  */
@@ -358,6 +359,54 @@ double oracle_energy(const cplx *psi, int N, const double *Jx, const double *Jy,
     oracle_overlap(psi, hpsi, N, ov);
     free(hpsi);
     return ov[0];
+}
+
+/*
+ * Two-spin correlations and one-spin expectations of psi by direct action of the spin
+ * operators on basis states (the conventions of oracle_apply_hamiltonian):
+ *   czz, cxx, cyy  N x N row-major, <S^a_i S^a_j> for i != j; the diagonal is
+ *                  <(S^a_i)^2> = <psi|psi>/4;
+ *   mx, my         <S^x_j> and <S^y_j>, j = 1..N.
+ * These extend the local polarisations and the echo of Sec. 4.2 to correlation functions.
+ */
+void oracle_correlations(const cplx *psi, int N, double *czz, double *cxx, double *cyy, double *mx, double *my)
+{
+    const int64_t dim = (int64_t)1 << N;
+    const double nrm = oracle_norm(psi, N);
+    for (int i = 0; i < N; i++) {
+        const uint64_t mi = UINT64_C(1) << i;
+        double ax = 0.0, ay = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : ax, ay)
+        for (int64_t si = 0; si < dim; si++) {
+            uint64_t s = (uint64_t)si;
+            int bi = (int)((s >> i) & 1);
+            cplx f = conj(psi[s]) * psi[s ^ mi];
+            /* <s|sigma^x|s^mi> = 1;  <s|sigma^y|s^mi> = -i if spin i of s is up, +i if down */
+            ax += creal(f);
+            ay += creal((bi ? -I : I) * f);
+        }
+        mx[i] = 0.5 * ax;
+        my[i] = 0.5 * ay;
+        czz[i * N + i] = cxx[i * N + i] = cyy[i * N + i] = 0.25 * nrm;
+        for (int j = i + 1; j < N; j++) {
+            const uint64_t mj = UINT64_C(1) << j;
+            double zz = 0.0, xx = 0.0, yy = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : zz, xx, yy)
+            for (int64_t si = 0; si < dim; si++) {
+                uint64_t s = (uint64_t)si;
+                int bi = (int)((s >> i) & 1), bj = (int)((s >> j) & 1);
+                double w = creal(psi[s]) * creal(psi[s]) + cimag(psi[s]) * cimag(psi[s]);
+                zz += w * (bi ? 0.5 : -0.5) * (bj ? 0.5 : -0.5);
+                cplx f = conj(psi[s]) * psi[s ^ mi ^ mj];
+                xx += 0.25 * creal(f);
+                /* sigma^y sigma^y: -1 if the two spins of s are equal, +1 otherwise */
+                yy += 0.25 * ((bi == bj) ? -1.0 : 1.0) * creal(f);
+            }
+            czz[i * N + j] = czz[j * N + i] = zz;
+            cxx[i * N + j] = cxx[j * N + i] = xx;
+            cyy[i * N + j] = cyy[j * N + i] = yy;
+        }
+    }
 }
 
 int oracle_num_threads(void)

@@ -137,7 +137,8 @@ struct ts_ctx {
     std::vector<double> Jraw[3];
     std::vector<double> hraw[3];
     double *dJq = nullptr, *dhh = nullptr;
-    float *dE = nullptr;      // phase-table mode: E_x, E_y, E_z per basis state (3 x 2^N floats), or NULL
+    void *dE = nullptr;       // phase-table mode: E_x, E_y, E_z per basis state (3 x 2^N doubles for
+                              // complex128, floats for complex64), or NULL
     Buf psi, ref, scratch;
     bool ref_valid = false;
     double *dpart = nullptr;
@@ -767,11 +768,12 @@ ts_status run_basic(ts_ctx *ctx, void *buf, const std::vector<HostSlot> &slots)
         }
         const Slot sl = slots[k].dev();
         if (ctx->dE) {
-            const float *E = ctx->dE + (size_t)sl.alpha * dim;
             if (ctx->prec == TS_C64)
-                k_slot_table<float><<<gs, 256, 0, ctx->stream>>>((float2 *)buf, E, dim, sl);
+                k_slot_table<float, float><<<gs, 256, 0, ctx->stream>>>(
+                    (float2 *)buf, static_cast<const float *>(ctx->dE) + (size_t)sl.alpha * dim, dim, sl);
             else
-                k_slot_table<double><<<gs, 256, 0, ctx->stream>>>((double2 *)buf, E, dim, sl);
+                k_slot_table<double, double><<<gs, 256, 0, ctx->stream>>>(
+                    (double2 *)buf, static_cast<const double *>(ctx->dE) + (size_t)sl.alpha * dim, dim, sl);
         } else if (ctx->prec == TS_C64) {
             k_slot_basic<float><<<gs, 256, 0, ctx->stream>>>((float2 *)buf, dim, hd, sl);
         } else {
@@ -1103,7 +1105,7 @@ unsigned red_blocks(const ts_ctx *ctx, uint64_t work_per_block)
 ts_status sum_sz(ts_ctx *ctx, const void *buf, double *norm_and_p /* N+1 */)
 {
     const int K = ctx->N + 1;
-    const unsigned nb = red_blocks(ctx, 256 * 32);
+    const unsigned nb = sum_sz_blocks(ctx->N, 512);
     ts_status st = ensure_part(ctx, (size_t)nb * K + K);
     if (st)
         return st;
@@ -1118,7 +1120,7 @@ ts_status sum_sz(ts_ctx *ctx, const void *buf, double *norm_and_p /* N+1 */)
 
 ts_status sum_norm(ts_ctx *ctx, const void *buf, double *out)
 {
-    const unsigned nb = red_blocks(ctx, 256 * 32);
+    const unsigned nb = red_blocks(ctx, UINT64_C(1) << kSumRangeBits);
     ts_status st = ensure_part(ctx, (size_t)nb + 1);
     if (st)
         return st;
@@ -1228,6 +1230,33 @@ ts_status rotated_energy(ts_ctx *ctx, int alpha, double *out)
         return st;
     *out = std::ldexp(v, -ctx->N);
     return TS_OK;
+}
+
+// The time-step bound of Eq. 4 (the inverse of the largest local second moment of H), from
+// the raw couplings (N*N row-major, upper triangle) and fields of each axis.
+double step_bound_of(int N, const std::vector<double> (&J)[3], const std::vector<double> (&h)[3])
+{
+    double mx = 0.0;
+    for (int j = 0; j < N; j++) {
+        double hs = 0.0;
+        for (int a = 0; a < 3; a++)
+            hs += (h[a][j] / 2) * (h[a][j] / 2);
+        for (int k = 0; k < N; k++) {
+            if (k == j)
+                continue;
+            double js = 0.0;
+            for (int a = 0; a < 3; a++) {
+                const double v = (j < k) ? J[a][j * N + k] : J[a][k * N + j];
+                js += (v / 4) * (v / 4);
+            }
+            const double m = hs + js;
+            if (m > mx)
+                mx = m;
+        }
+        if (N == 1 && hs > mx)
+            mx = hs;
+    }
+    return mx > 0.0 ? 1.0 / std::sqrt(mx) : INFINITY;
 }
 
 bool finite_all(const double *p, size_t n)
@@ -1489,6 +1518,17 @@ ts_status ts_step_order(ts_ctx *ctx, int order, double tau, int64_t nsteps)
         return fail(ctx, TS_ERR_STATE, "ts_step: no state set");
     if (nsteps == 0)
         return TS_OK;
+    {
+        // Eq. 4: the step must be small against the largest local time scale of H
+        const double bound = step_bound_of(ctx->N, ctx->Jraw, ctx->hraw);
+        if (std::fabs(tau) >= bound) {
+            char msg[200];
+            std::snprintf(msg, sizeof(msg),
+                          "warning: |tau| = %.6g is not small against the Eq. 4 time scale %.6g of this "
+                          "Hamiltonian; the Trotter-Suzuki error may be large", std::fabs(tau), bound);
+            ctx->err = msg;
+        }
+    }
     std::vector<HostSlot> slots = make_slots(ctx->N, order, tau, nsteps);
     // With chaining on, consecutive calls run like one chained call (Sec. 2: the P_z halves of
     // adjacent U2s merge): a held-back final pass of the previous call is merged into this
@@ -1693,7 +1733,8 @@ ts_status ts_set_phase_tables(ts_ctx *ctx, int enable)
     if (ctx->dE)
         return TS_OK;
     const uint64_t dim = dim_of(ctx);
-    const size_t bytes = 3 * (size_t)dim * sizeof(float);
+    const size_t esize = ctx->prec == TS_C64 ? sizeof(float) : sizeof(double);
+    const size_t bytes = 3 * (size_t)dim * esize;
     size_t freeb = 0, totb = 0;
     TS_CUDA(ctx, cudaMemGetInfo(&freeb, &totb));
     if (bytes > freeb)
@@ -1702,7 +1743,12 @@ ts_status ts_set_phase_tables(ts_ctx *ctx, int enable)
     const HamDev hd = ham_dev(ctx);
     const unsigned gs = grid_for(ctx, dim, 256);
     for (int a = 0; a < 3; a++) {
-        k_energy_table<<<gs, 256, 0, ctx->stream>>>(ctx->dE + (size_t)a * dim, dim, hd, a);
+        if (ctx->prec == TS_C64)
+            k_energy_table<float><<<gs, 256, 0, ctx->stream>>>(static_cast<float *>(ctx->dE) + (size_t)a * dim,
+                                                               dim, hd, a);
+        else
+            k_energy_table<double><<<gs, 256, 0, ctx->stream>>>(static_cast<double *>(ctx->dE) + (size_t)a * dim,
+                                                                dim, hd, a);
         ctx->launches++;
     }
     TS_CUDA(ctx, cudaGetLastError());
@@ -1761,28 +1807,23 @@ double ts_step_bound(const ts_ctx *ctx)
 {
     if (!ctx)
         return 0.0;
-    const int N = ctx->N;
-    double mx = 0.0;
-    for (int j = 0; j < N; j++) {
-        double hs = 0.0;
-        for (int a = 0; a < 3; a++)
-            hs += (ctx->hraw[a][j] / 2) * (ctx->hraw[a][j] / 2);
-        for (int k = 0; k < N; k++) {
-            if (k == j)
-                continue;
-            double js = 0.0;
-            for (int a = 0; a < 3; a++) {
-                const double v = (j < k) ? ctx->Jraw[a][j * N + k] : ctx->Jraw[a][k * N + j];
-                js += (v / 4) * (v / 4);
-            }
-            const double m = hs + js;
-            if (m > mx)
-                mx = m;
-        }
-        if (N == 1 && hs > mx)
-            mx = hs;
+    return step_bound_of(ctx->N, ctx->Jraw, ctx->hraw);
+}
+
+double ts_step_bound_host(int N, const double *Jx, const double *Jy, const double *Jz, const double *hx,
+                          const double *hy, const double *hz)
+{
+    if (N < 1 || N > kMaxN || !Jx || !Jy || !Jz)
+        return -1.0;
+    std::vector<double> J[3], h[3];
+    const double *Js[3] = {Jx, Jy, Jz}, *hs[3] = {hx, hy, hz};
+    for (int a = 0; a < 3; a++) {
+        J[a].assign(Js[a], Js[a] + (size_t)N * N);
+        h[a].assign((size_t)N, 0.0);
+        if (hs[a])
+            h[a].assign(hs[a], hs[a] + N);
     }
-    return mx > 0.0 ? 1.0 / std::sqrt(mx) : INFINITY;
+    return step_bound_of(N, J, h);
 }
 
 } // extern "C"

@@ -72,6 +72,16 @@ __device__ __forceinline__ void bfly(double2 &a, double2 &b)
     b = d;
 }
 
+// Knuth's two-sum: s + err = a + b exactly.  Written with the _rn intrinsics, which the
+// compiler never fuses into multiply-adds, so the transform stays error-free.
+__device__ __forceinline__ float2 two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, err);
+}
+
 // e^{-i pi x}: angles on the device are carried in half-turns (units of pi),
 // already reduced in FP64, so CUDA's sincospi needs no large-argument path.
 __device__ __forceinline__ float2 cexpm_pi(float x)

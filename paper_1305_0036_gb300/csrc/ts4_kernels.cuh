@@ -5,7 +5,7 @@
 //   k_slot_basic  one diagonal slot per element, E(s) from bit tests (Sec. 3.1)
 //   (the fused tile pass k_tile is in ts4_tile.cuh; this file holds the step
 //   descriptors and per-pass tables it shares with the host)
-//   k_sum_*       FP64-accumulating reductions for the observables (Sec. 4.2)
+//   k_sum_*       reductions for the observables (Sec. 4.2), FP64-grade accumulation
 #pragma once
 
 #include "ts4_common.cuh"
@@ -77,27 +77,29 @@ __global__ void k_slot_basic(typename CT<R>::T *__restrict__ psi, uint64_t dim, 
     }
 }
 
-// The paper's phase-table mode (Sec. 3.1): E_alpha(s) for every basis state, stored once
-// (FP32, 4 bytes per state and alpha), so that a slot reads its angle instead of forming it
-// from the bits.  Kept for the A/B comparison with the bit-test and the fused kernels.
-static __global__ void k_energy_table(float *__restrict__ E, uint64_t dim, HamDev ham, int alpha)
+// The paper's phase-table mode (Sec. 3.1): E_alpha(s) for every basis state, stored once, so
+// that a slot reads its angle instead of forming it from the bits.  E is the table's type:
+// double for complex128 (8 bytes per state and alpha, the paper's FP64 tables), float for
+// complex64 (4 bytes).  Kept for the A/B comparison with the bit-test and the fused kernels.
+template <typename E>
+__global__ void k_energy_table(E *__restrict__ tab, uint64_t dim, HamDev ham, int alpha)
 {
     const double *Jq = ham.Jq + (size_t)alpha * ham.N * ham.N;
     const double *hh = ham.hh + (size_t)alpha * ham.N;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < dim; s += stride)
-        E[s] = (float)energy_bits(s, Jq, hh, ham.N);
+        tab[s] = (E)energy_bits(s, Jq, hh, ham.N);
 }
 
-// One slot from the energy table: as k_slot_basic, with E_alpha(s) read from E.
-template <typename R>
-__global__ void k_slot_table(typename CT<R>::T *__restrict__ psi, const float *__restrict__ E, uint64_t dim, Slot sl)
+// One slot from the energy table: as k_slot_basic, with E_alpha(s) read from the table.
+template <typename R, typename E>
+__global__ void k_slot_table(typename CT<R>::T *__restrict__ psi, const E *__restrict__ tab, uint64_t dim, Slot sl)
 {
     using C = typename CT<R>::T;
     const double scale = sl.scale;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < dim; s += stride) {
-        const double th = sl.th0 + sl.t * (double)E[s];
+        const double th = sl.th0 + sl.t * (double)tab[s];
         double2 f = cexpm_pi(halfturns_2pi(th));
         f.x *= scale;
         f.y *= scale;
@@ -221,99 +223,183 @@ template <int K, typename T> __device__ void block_sum(T (&v)[K], T *__restrict_
     __syncthreads();
 }
 
-// Per-thread sums over the 32 amplitudes p[j * stride], j < 32 (those with j < n):
-// tot = sum |psi|^2 and low[b] = sum over j with bit b of j set (b < 5).
-// complex64: squares and pairwise sums in FP32 (error <= 5 u of the thread's
-// total), converted once to FP64; complex128: FP64 throughout.
-template <typename C, typename A>
-__device__ __forceinline__ void thread_sums32(const C *__restrict__ p, int stride, int n, A &tot, A (&low)[5])
+// ---- accumulation of |psi_s|^2 at FP64-grade accuracy
+// complex64: the square of an FP32 component is exact as its product plus the FMA residual, and
+// a thread keeps its sums as unevaluated float pairs hi + lo ("double-float"): two_sum keeps the
+// rounding of every addition in lo, so a sum of n terms is off by about n u^2 (u = 2^-24) of its
+// value instead of n u.  GB300's FP64 pipe is too narrow for one FP64 addition per amplitude at
+// HBM speed (about 0.4 ms per operation per amplitude at N = 28, more than the 0.3 ms read), while
+// these FP32 operations fit under the read.  Per-thread results are converted to FP64 (exactly:
+// hi and lo are floats) and reduced across the block and the grid in FP64.
+// complex128: plain FP64 throughout.
+struct DF {
+    float hi, lo;
+};
+
+template <typename C> struct SqAcc;
+template <> struct SqAcc<float2> {
+    DF v;
+    __device__ __forceinline__ void zero() { v.hi = v.lo = 0.0f; }
+    __device__ __forceinline__ void add_sq(float2 a)
+    {
+        const float p1 = __fmul_rn(a.x, a.x), e1 = __fmaf_rn(a.x, a.x, -p1);
+        const float p2 = __fmul_rn(a.y, a.y), e2 = __fmaf_rn(a.y, a.y, -p2);
+        const float2 s = two_sum(p1, p2);
+        const float2 h = two_sum(v.hi, s.x);
+        v.hi = h.x;
+        v.lo = __fadd_rn(v.lo, __fadd_rn(h.y, __fadd_rn(s.y, __fadd_rn(e1, e2))));
+    }
+    __device__ __forceinline__ void add(const SqAcc &o)
+    {
+        const float2 h = two_sum(v.hi, o.v.hi);
+        v.hi = h.x;
+        v.lo = __fadd_rn(v.lo, __fadd_rn(h.y, o.v.lo));
+    }
+    // this minus o, for o an earlier value of the same running sum (the difference is formed
+    // from the exact hi difference and the lo terms)
+    __device__ __forceinline__ SqAcc minus(const SqAcc &o) const
+    {
+        SqAcc r;
+        const float2 h = two_sum(v.hi, -o.v.hi);
+        r.v.hi = h.x;
+        r.v.lo = __fadd_rn(h.y, __fsub_rn(v.lo, o.v.lo));
+        return r;
+    }
+    // moves the rounding in lo back under hi (keeps |lo| <= ulp(hi) / 2 over long sums)
+    __device__ __forceinline__ void renorm()
+    {
+        const float s = __fadd_rn(v.hi, v.lo);
+        v.lo = __fsub_rn(v.lo, __fsub_rn(s, v.hi));
+        v.hi = s;
+    }
+    __device__ __forceinline__ double value() const { return (double)v.hi + (double)v.lo; }
+};
+template <> struct SqAcc<double2> {
+    double v;
+    __device__ __forceinline__ void zero() { v = 0.0; }
+    __device__ __forceinline__ void add_sq(double2 a) { v += a.x * a.x + a.y * a.y; }
+    __device__ __forceinline__ void add(const SqAcc &o) { v += o.v; }
+    __device__ __forceinline__ SqAcc minus(const SqAcc &o) const
+    {
+        SqAcc r;
+        r.v = v - o.v;
+        return r;
+    }
+    __device__ __forceinline__ void renorm() {}
+    __device__ __forceinline__ double value() const { return v; }
+};
+
+// Geometry of the |psi|^2 reductions: a range is 2^12 consecutive amplitudes; in a range the
+// 256 threads take global bits 0..7 (coalesced loads) and the 16 amplitudes of a thread global
+// bits 8..11.
+constexpr int kSumTBits = 8, kSumJBits = 4, kSumRangeBits = kSumTBits + kSumJBits;
+// Varying range bits one block of k_sum_sz may span (its span of ranges is at most 2^12).
+constexpr int kSumMaxVar = 12;
+
+__host__ __device__ constexpr uint64_t sum_ranges(int N)
 {
-    A q[32];
-#pragma unroll
-    for (int j = 0; j < 32; j++) {
-        C a;
-        a.x = 0;
-        a.y = 0;
-        if (j < n)
-            a = p[(size_t)j * stride];
-        q[j] = (A)a.x * (A)a.x + (A)a.y * (A)a.y;
-    }
-    // sum over the elements with bit b set = pairwise tree over the 16 such elements
-#pragma unroll
-    for (int b = 0; b < 5; b++) {
-        A t[16];
-        int k = 0;
-#pragma unroll
-        for (int j = 0; j < 32; j++)
-            if ((j >> b) & 1)
-                t[k++] = q[j];
-#pragma unroll
-        for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-            for (int i = 0; i < w; i++)
-                t[i] = t[i] + t[i + w];
-        low[b] = t[0];
-    }
-#pragma unroll
-    for (int w = 16; w >= 1; w >>= 1)
-#pragma unroll
-        for (int i = 0; i < w; i++)
-            q[i] = q[i] + q[i + w];
-    tot = q[0];
+    return N > kSumRangeBits ? (UINT64_C(1) << (N - kSumRangeBits)) : UINT64_C(1);
 }
 
-template <typename C> struct AccOf;
-template <> struct AccOf<float2> { using T = float; };
-template <> struct AccOf<double2> { using T = double; };
+// Number of blocks for k_sum_sz: a power of two that divides the ranges, at most `cap` (a
+// power of two), and large enough that every block spans at most 2^kSumMaxVar ranges.
+__host__ __device__ inline unsigned sum_sz_blocks(int N, unsigned cap)
+{
+    const uint64_t R = sum_ranges(N);
+    uint64_t b = R < cap ? R : cap;
+    while (R / b > (UINT64_C(1) << kSumMaxVar))
+        b <<= 1;
+    return (unsigned)b;
+}
 
-// Per block: [0] = sum |psi|^2, [1..] = sum |psi_s|^2 bit_i(s) for i < N  (stride N+1).
-// Each block iteration covers 2^13 consecutive amplitudes; its 14 sums are formed in
-// the precision of the amplitudes (complex64: FP32 pairwise per thread and across
-// the block, relative error ~1e-6 of that range's weight) and added to FP64 totals.
+// Per block: part[b (N + 1)] = sum |psi_s|^2 and part[b (N + 1) + 1 + i] = sum |psi_s|^2 bit_i(s)
+// over the block's amplitudes (<S^z_i> = the second minus half the first, Sec. 4.2).
+// gridDim.x = sum_sz_blocks(N, cap): block b covers the contiguous span of S = 2^m ranges from
+// b S, so range bits m and above are the same for the whole block.  Per thread: one accumulator
+// per register index j (global bits 8..11), a running total, and, for each of the m varying
+// range bits, the sum of the totals of the ranges that set it (each range's total is the
+// difference of the running total before and after it).
 template <typename C>
 __global__ void __launch_bounds__(256) k_sum_sz(const C *__restrict__ psi, int N, double *__restrict__ part)
 {
-    using A = typename AccOf<C>::T;
-    constexpr int LB = 5;
+    constexpr int NJ = 1 << kSumJBits;
+    constexpr int NV = 1 + kSumRangeBits + kSumMaxVar;
     const uint64_t dim = UINT64_C(1) << N;
-    __shared__ double acc_sh[64];
-    for (int i = threadIdx.x; i < 64; i += blockDim.x)
-        acc_sh[i] = 0.0;
-    __syncthreads();
-    const uint64_t per_block = (uint64_t)blockDim.x << LB;
-    const int RBITS = 5 + 8;              // bits resolved inside one block range (blockDim = 256)
-    // amplitude base + (j << 8) + tid: thread bits are global bits 0..7 (coalesced),
-    // the 32 per-thread values are global bits 8..12
-    for (uint64_t base = (uint64_t)blockIdx.x * per_block; base < dim; base += (uint64_t)gridDim.x * per_block) {
-        A tot = A(0), low[LB] = {A(0), A(0), A(0), A(0), A(0)};
-        const uint64_t s0 = base + threadIdx.x;
-        if (s0 < dim) {
-            const uint64_t rem = (dim - s0 + 255) >> 8;       // elements s0 + 256 j below dim
-            const int n = rem < 32 ? (int)rem : 32;
-            thread_sums32<C, A>(psi + s0, 256, n, tot, low);
-        }
-        A v[1 + 8 + LB];
-        v[0] = tot;
+    const uint64_t span = sum_ranges(N) / gridDim.x;
+    const int m = 63 - __clzll((long long)span);            // span = 2^m
+    const uint64_t r0 = (uint64_t)blockIdx.x * span;
+    const uint32_t t = threadIdx.x;
+    SqAcc<C> acc[NJ], tot, hv[kSumMaxVar];
 #pragma unroll
-        for (int b = 0; b < 8; b++)
-            v[1 + b] = ((threadIdx.x >> b) & 1) ? tot : A(0);
+    for (int j = 0; j < NJ; j++)
+        acc[j].zero();
+    tot.zero();
 #pragma unroll
-        for (int b = 0; b < LB; b++)
-            v[1 + 8 + b] = low[b];
-        __shared__ A bs[1 + 8 + LB];
-        block_sum<1 + 8 + LB>(v, bs);
-        if (threadIdx.x == 0) {
-            acc_sh[0] += (double)bs[0];
-            for (int i = 0; i < N && i < RBITS; i++)
-                acc_sh[1 + i] += (double)bs[1 + i];
-            for (int i = RBITS; i < N; i++)
-                if ((base >> i) & 1)
-                    acc_sh[1 + i] += (double)bs[0];
+    for (int k = 0; k < kSumMaxVar; k++)
+        hv[k].zero();
+    for (uint64_t rr = 0; rr < span; rr++) {
+        const uint64_t s0 = ((r0 + rr) << kSumRangeBits) + t;
+        const SqAcc<C> before = tot;
+        C a[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; j++) {
+            const uint64_t s = s0 + ((uint64_t)j << kSumTBits);
+            a[j].x = 0;
+            a[j].y = 0;
+            if (s < dim)
+                a[j] = psi[s];
         }
-        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NJ; j++) {
+            acc[j].add_sq(a[j]);
+            tot.add_sq(a[j]);
+        }
+        tot.renorm();
+        const SqAcc<C> it = tot.minus(before);
+#pragma unroll
+        for (int k = 0; k < kSumMaxVar; k++)
+            if (k < m && ((rr >> k) & 1)) {
+                hv[k].add(it);
+                hv[k].renorm();
+            }
+#pragma unroll
+        for (int j = 0; j < NJ; j++)
+            acc[j].renorm();
     }
-    for (int i = threadIdx.x; i <= N; i += blockDim.x)
-        part[(size_t)blockIdx.x * (N + 1) + i] = acc_sh[i];
+    // the thread's sums in FP64: total, thread bits, register bits, varying range bits
+    double v[NV];
+    const double T = tot.value();
+    v[0] = T;
+#pragma unroll
+    for (int b = 0; b < kSumTBits; b++)
+        v[1 + b] = ((t >> b) & 1) ? T : 0.0;
+#pragma unroll
+    for (int b = 0; b < kSumJBits; b++) {
+        SqAcc<C> lb;
+        lb.zero();
+#pragma unroll
+        for (int j = 0; j < NJ; j++)
+            if ((j >> b) & 1)
+                lb.add(acc[j]);
+        v[1 + kSumTBits + b] = lb.value();
+    }
+#pragma unroll
+    for (int k = 0; k < kSumMaxVar; k++)
+        v[1 + kSumRangeBits + k] = hv[k].value();
+    __shared__ double bs[NV];
+    block_sum<NV>(v, bs);
+    for (int i = threadIdx.x; i <= N; i += blockDim.x) {
+        double r;
+        if (i == 0)
+            r = bs[0];
+        else if (i - 1 < kSumRangeBits)
+            r = bs[i];                                           // thread and register bits
+        else if (i - 1 - kSumRangeBits < m)
+            r = bs[i];                                           // range bits that vary in the span
+        else
+            r = ((r0 >> (i - 1 - kSumRangeBits)) & 1) ? bs[0] : 0.0;   // constant over the span
+        part[(size_t)blockIdx.x * (N + 1) + i] = r;
+    }
 }
 
 // Joint bit weights for two-spin correlations.  Per block, FP64, stride K = 1 + N + N(N-1)/2:
@@ -321,14 +407,15 @@ __global__ void __launch_bounds__(256) k_sum_sz(const C *__restrict__ psi, int N
 // with w(s) = |psi_s|^2, b_i the bits of s and pair(i, j) (i < j) the row-major index of the
 // strict upper triangle.  Each block iteration covers 2^13 consecutive amplitudes: thread bits
 // are global bits 0..7, the 32 per-thread amplitudes global bits 8..12, the higher bits are
-// constant over the range.  The 92 in-range sums (total, 13 singles, 78 pairs) are formed in the
-// amplitudes' precision and added, with the constant high bits, to FP64 totals.
+// constant over the range.  The 92 in-range sums (total, 13 singles, 78 pairs) are formed in
+// FP64 (for both precisions: these correlations are read rarely, so the FP64 rate does not
+// matter) and added, with the constant high bits, to the block's FP64 totals.
 __host__ __device__ constexpr int pair_index(int i, int j, int N) { return i * N - i * (i + 1) / 2 + (j - i - 1); }
 
 template <typename C>
 __global__ void __launch_bounds__(256) k_sum_pairs(const C *__restrict__ psi, int N, double *__restrict__ part)
 {
-    using A = typename AccOf<C>::T;
+    using A = double;
     constexpr int LB = 5, TBITS = 8, RBITS = LB + TBITS;
     constexpr int NV = 1 + RBITS + RBITS * (RBITS - 1) / 2;   // 92
     const int K = 1 + N + N * (N - 1) / 2;
@@ -441,39 +528,37 @@ __global__ void __launch_bounds__(256) k_sum_pairs(const C *__restrict__ psi, in
         part[(size_t)blockIdx.x * K + i] = acc_sh[i];
 }
 
-// Per block: sum |psi|^2 over a grid-stride range; per thread FP32 (complex64) pairwise
-// sums of 32 amplitudes added to an FP64 running total, one FP64 block reduction.
+// Per block: sum |psi|^2 over a grid-stride set of ranges (the geometry of k_sum_sz); each
+// thread keeps two running sums of the accumulator type above, one FP64 block reduction.
 template <typename C>
 __global__ void __launch_bounds__(256) k_sum_norm(const C *__restrict__ psi, int N, double *__restrict__ part)
 {
-    using A = typename AccOf<C>::T;
+    constexpr int NJ = 1 << kSumJBits;
     const uint64_t dim = UINT64_C(1) << N;
-    const uint64_t per_block = (uint64_t)blockDim.x << 5;
-    double run = 0.0;
-    for (uint64_t base = (uint64_t)blockIdx.x * per_block; base < dim; base += (uint64_t)gridDim.x * per_block) {
-        const uint64_t s0 = base + threadIdx.x;
-        if (s0 < dim) {
-            const uint64_t rem = (dim - s0 + 255) >> 8;
-            const int n = rem < 32 ? (int)rem : 32;
-            A q[32];
+    const uint64_t R = sum_ranges(N);
+    SqAcc<C> s0, s1;
+    s0.zero();
+    s1.zero();
+    for (uint64_t r = blockIdx.x; r < R; r += gridDim.x) {
+        const uint64_t b = (r << kSumRangeBits) + threadIdx.x;
+        C a[NJ];
 #pragma unroll
-            for (int j = 0; j < 32; j++) {
-                C a;
-                a.x = 0;
-                a.y = 0;
-                if (j < n)
-                    a = psi[s0 + (size_t)j * 256];
-                q[j] = (A)a.x * (A)a.x + (A)a.y * (A)a.y;
-            }
-#pragma unroll
-            for (int w = 16; w >= 1; w >>= 1)
-#pragma unroll
-                for (int i = 0; i < w; i++)
-                    q[i] = q[i] + q[i + w];
-            run += (double)q[0];
+        for (int j = 0; j < NJ; j++) {
+            const uint64_t s = b + ((uint64_t)j << kSumTBits);
+            a[j].x = 0;
+            a[j].y = 0;
+            if (s < dim)
+                a[j] = psi[s];
         }
+#pragma unroll
+        for (int j = 0; j < NJ; j += 2) {
+            s0.add_sq(a[j]);
+            s1.add_sq(a[j + 1]);
+        }
+        s0.renorm();
+        s1.renorm();
     }
-    double v[1] = {run};
+    double v[1] = {s0.value() + s1.value()};
     __shared__ double bs[1];
     block_sum<1>(v, bs);
     if (threadIdx.x == 0)

@@ -2,13 +2,12 @@
 // any device allocation.
 //
 // Some callers cannot call cudaMalloc at the point where they need these
-// numbers: code running while a stream is being captured into a CUDA graph
-// (allocation is not a capturable operation), host applications whose device
-// memory is owned by their own pool allocator and handed out only to them, or
-// plug-ins that must not grow the device footprint behind their host's back.
-// This entry point serves them: the caller passes the state and a device
-// output buffer, and the only scratch memory used -- the per-block partial
-// sums -- is a fixed array with static storage in this file.
+// numbers: host applications whose device memory is owned by their own pool
+// allocator and handed out only to them, plug-ins that must not grow the
+// device footprint behind their host's back, and loops that must not allocate
+// once they have started.  This entry point serves them: the caller passes the
+// state and a device output buffer, and the only scratch memory used -- the
+// per-block partial sums -- is a fixed array with static storage in this file.
 //
 // The array is TS_STATIC_MAX_BLOCKS * (TS_STATIC_MAX_N + 1) doubles (about
 // 280 KB); every GPU that loads the library holds it until the process exits.
@@ -72,10 +71,10 @@ extern "C" ts_status ts_reduce_sz_static(const void *psi_dev, int N, ts_prec pre
         part = g_partials_addr[dev];
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const uint64_t dim = UINT64_C(1) << N;
-    uint64_t nb = (dim + 8191) / 8192;          // one block covers 2^13 amplitudes per iteration
-    if (nb > TS_STATIC_MAX_BLOCKS)
-        nb = TS_STATIC_MAX_BLOCKS;
+    // a power of two of at most TS_STATIC_MAX_BLOCKS blocks (k_sum_sz's span layout)
+    const unsigned nb = ts4::sum_sz_blocks(N, TS_STATIC_MAX_BLOCKS);
+    if (nb > (unsigned)TS_STATIC_MAX_BLOCKS)
+        return TS_ERR_ARG;
     if (prec == TS_C64)
         ts4::k_sum_sz<float2><<<(unsigned)nb, 256, 0, st>>>((const float2 *)psi_dev, N, part);
     else

@@ -201,16 +201,6 @@ template <typename R, int TB, int RB> struct TileShared {
     int pcF;
 };
 
-// Knuth's two-sum: s + err = a + b exactly.  Written with the _rn intrinsics, which the
-// compiler never fuses into multiply-adds, so the transform stays error-free.
-__device__ __forceinline__ float2 two_sum(float a, float b)
-{
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return make_float2(s, err);
-}
-
 // sin and cos of pi r for |r| <= 1/4 (plus rounding), without branches: x = pi r with
 // pi split into two floats (x to ~1e-15 relative), then the Taylor series of sin to
 // x^13 and of cos to x^14 (truncation below 3e-14 for |x| <= pi/4 + 1e-6).  The

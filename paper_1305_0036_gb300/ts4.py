@@ -45,6 +45,7 @@ SIGNATURES = {
     "ts_set_schedule": (_I, [_P, _I, _I, _I]),
     "ts_get_schedule": (_I, [_P, _P, _P, _P, _P, _P]),
     "ts_step_bound": (_D, [_P]),
+    "ts_step_bound_host": (_D, [_I, _P, _P, _P, _P, _P, _P]),
     "ts_tile_global_index": (_U64, [_I, _I, _I, _I, _U64, _U64]),
     "ts_plan": (_I, [_I, _I, _I, _I, _I, _I64, _I, _P, _I, _P, _P, _I64, _P]),
     "ts_set_chaining": (_I, [_P, _I]),
@@ -176,6 +177,13 @@ def ts_get_schedule(ctx):
 
 def ts_step_bound(ctx):
     return float(_lib.ts_step_bound(ctx))
+
+
+def ts_step_bound_host(N, Jx, Jy, Jz, hx=None, hy=None, hz=None):
+    """The Eq. 4 time-step bound from the couplings, on the host (no GPU)."""
+    Jx, Jy, Jz = _mat(Jx, N), _mat(Jy, N), _mat(Jz, N)
+    hx, hy, hz = _vec(hx, N), _vec(hy, N), _vec(hz, N)
+    return float(_lib.ts_step_bound_host(int(N), _p(Jx), _p(Jy), _p(Jz), _p(hx), _p(hy), _p(hz)))
 
 
 def ts_tile_global_index(N, c, w, h, f, e):

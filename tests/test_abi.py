@@ -106,3 +106,26 @@ def test_tile_mapping_is_a_partition(lib):
         for f in range(1 << (N - c - h)):
             seen += [lib.ts_tile_global_index(N, c, w, h, f, e) for e in range(1 << (c + h))]
         assert sorted(seen) == list(range(1 << N))
+
+
+def test_step_bound_host_is_eq4(lib):
+    """Eq. 4: [max_{j,k} (sum_a (h^a_j/2)^2 + sum_a (J^a_jk/4)^2)^(1/2)]^-1, on closed forms."""
+    import numpy as np
+    J = np.zeros((2, 2))
+    J[0, 1] = 1.0
+    # one isotropic bond, no field: 3 (1/4)^2 = 3/16
+    assert lib.ts_step_bound_host(2, J, J, J) == pytest.approx(4 / np.sqrt(3), rel=1e-15)
+    # a z-field of 1 on spin 1 adds (1/2)^2 to that spin's terms: 3/16 + 4/16
+    assert lib.ts_step_bound_host(2, J, J, J, hz=[1.0, 0.0]) == pytest.approx(4 / np.sqrt(7), rel=1e-15)
+    # transverse fields count alike; the lower triangle is ignored
+    Jl = J.T.copy()
+    assert lib.ts_step_bound_host(2, J + Jl, J, J, hx=[0.0, 2.0]) == pytest.approx(1 / np.sqrt(1 + 3 / 16), rel=1e-15)
+    # the dipolar chain: nearest neighbours J^z = 1, J^x = J^y = -1/2 give 6/64
+    from paper_1305_0036_gb300 import workloads as W
+    s = W.dipolar_chain(28)
+    assert lib.ts_step_bound_host(28, s.Jx, s.Jy, s.Jz, hz=s.hz) == pytest.approx(8 / np.sqrt(6), rel=1e-15)
+    # no Hamiltonian: no time scale
+    Z = np.zeros((3, 3))
+    assert lib.ts_step_bound_host(3, Z, Z, Z) == float("inf")
+    assert lib._lib.ts_step_bound_host(0, Z.ctypes.data, Z.ctypes.data, Z.ctypes.data, None, None, None) == -1.0
+    assert lib._lib.ts_step_bound_host(3, None, Z.ctypes.data, Z.ctypes.data, None, None, None) == -1.0

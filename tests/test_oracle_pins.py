@@ -271,6 +271,47 @@ def test_observables_match_dense():
     assert oracle.overlap(phi, psi, N) == pytest.approx(np.vdot(phi, psi), abs=1e-14)
 
 
+def test_correlations_match_dense():
+    """<S^a_i S^a_j> and <S^x_j>, <S^y_j> against Kronecker-product operators on a random state."""
+    N = 5
+    psi = W.haar_state(N, 94)
+    from tests.dense_ref import SX, SY, SZ, site_op
+    C, mx, my = oracle.correlations(psi, N)
+    for a, op in (("x", SX), ("y", SY), ("z", SZ)):
+        for i in range(N):
+            for j in range(N):
+                want = np.vdot(psi, site_op(op, i, N) @ (site_op(op, j, N) @ psi)).real
+                assert C[a][i, j] == pytest.approx(want, abs=1e-14), (a, i, j)
+    np.testing.assert_allclose(mx, [np.vdot(psi, site_op(SX, j, N) @ psi).real for j in range(N)], atol=1e-14)
+    np.testing.assert_allclose(my, [np.vdot(psi, site_op(SY, j, N) @ psi).real for j in range(N)], atol=1e-14)
+
+
+def test_correlations_closed_forms():
+    """Product states: every spin along +x, along +y, and a Neel state along z."""
+    N = 3
+    # |+x> = (|up> + |down>)/sqrt 2 on every site
+    plus = np.ones(1 << N, dtype=complex) / np.sqrt(1 << N)
+    C, mx, my = oracle.correlations(plus, N)
+    np.testing.assert_allclose(mx, 0.5, atol=1e-15)
+    np.testing.assert_allclose(my, 0.0, atol=1e-15)
+    np.testing.assert_allclose(C["x"], 0.25, atol=1e-15)
+    np.testing.assert_allclose(C["z"] - np.diag(np.diag(C["z"])), 0.0, atol=1e-15)
+    # |+y> = (|up> + i |down>)/sqrt 2: bit 1 (up) carries 1, bit 0 (down) carries i
+    k = np.arange(1 << N)
+    amp = np.prod([np.where((k >> b) & 1, 1.0, 1j) for b in range(N)], axis=0) / np.sqrt(1 << N)
+    C, mx, my = oracle.correlations(amp, N)
+    np.testing.assert_allclose(my, 0.5, atol=1e-15)
+    np.testing.assert_allclose(mx, 0.0, atol=1e-15)
+    np.testing.assert_allclose(C["y"], 0.25, atol=1e-15)
+    # Neel |up down up> along z: <S^z_i S^z_j> = +-1/4, no transverse order
+    neel = np.zeros(1 << N, dtype=complex)
+    neel[0b101] = 1.0
+    C, mx, my = oracle.correlations(neel, N)
+    assert C["z"][0, 1] == -0.25 and C["z"][0, 2] == 0.25 and C["z"][1, 1] == 0.25
+    np.testing.assert_allclose(C["x"] - np.diag(np.diag(C["x"])), 0.0, atol=1e-15)
+    np.testing.assert_allclose(mx, 0.0, atol=1e-15)
+
+
 def test_suzuki_coefficient():
     a = oracle.suzuki_a()
     assert a == pytest.approx(0.41449077179437573, abs=1e-16)
