@@ -538,6 +538,42 @@ def run_ours(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_phase_table_ab(args):
+    """The paper's phase-table mode (Sec. 3.1) against bit tests and the fused pass: ms per TS4
+    step of the dipolar chain at each N in --ab-sizes, for both precisions (one JSON line)."""
+    import torch
+    from paper_1305_0036_gb300 import build
+    build.build()
+    from paper_1305_0036_gb300 import ts4, workloads as W
+    torch.cuda.set_device(0)
+    rows = []
+    for N in args.ab_sizes:
+        s = W.dipolar_chain(N)
+        for prec in ("c64", "c128"):
+            row = {"N": N, "prec": prec}
+            for mode in ("fused", "basic_bits", "basic_tables"):
+                ctx = ts4.Context.from_system(s, prec=prec)
+                if mode != "fused":
+                    ctx.set_schedule(ts4.TS_KERNEL_BASIC, 0, 0)
+                if mode == "basic_tables":
+                    ctx.set_phase_tables(True)
+                ctx.set_basis_state(W.neel_index(N))
+                ctx.step(TAU, 1)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                n = args.ab_steps
+                a.record(ctx.stream)
+                ctx.step(TAU, n)
+                b.record(ctx.stream)
+                torch.cuda.synchronize()
+                row[mode + "_ms"] = a.elapsed_time(b) / n
+                ctx.close()
+                torch.cuda.empty_cache()
+            rows.append(row)
+    print(json.dumps({"phase_table_ab": rows, "workload": "dipolar XXZ chain, Neel state, tau=0.01",
+                      "tables": "complex64: 3 x 2^N floats; complex128: 3 x 2^N doubles"}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -554,10 +590,17 @@ def main():
     ap.add_argument("--no-configs", action="store_true", help="skip the config-4 and config-5 lines")
     ap.add_argument("--validate-cpu-model", action="store_true",
                     help="also time one real oracle U1 at N=28 against its composition from the parts")
+    ap.add_argument("--phase-table-ab", action="store_true",
+                    help="time the paper's phase-table mode against bit tests and the fused pass instead")
+    ap.add_argument("--ab-sizes", type=int, nargs="+", default=[22, 26, 28])
+    ap.add_argument("--ab-steps", type=int, default=1)
     ap.add_argument("--spins", type=int, default=28,
                     help="chain length N (28 is the benchmark; smaller N only for profiling captures)")
     args = ap.parse_args()
     ws, rank, local = dist_init()
+    if args.phase_table_ab:
+        run_phase_table_ab(args)
+        return
     if args.impl == "reference":
         run_reference(args, ws, rank)
     else:

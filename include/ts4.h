@@ -336,9 +336,14 @@ TS4_API ts_status ts_reduce_sz_static(const void *psi_dev, int N, ts_prec prec, 
  * other (nstates[k] x 2^N[k] amplitudes).  This is the ensemble use of the
  * method for typical-state averages (App. A: random-phase states stand in for
  * the infinite-temperature density matrix).  Every system uses the same tile
- * size; at each pass index one kernel launch covers every state of every
- * system, and a whole ts_batch_step is captured into one CUDA graph and
- * replayed (the graph is rebuilt only when tau or nsteps change).
+ * size.  A whole ts_batch_step is one launch of a persistent kernel: its blocks
+ * take the (pass, state, tile) work items in pass-major order from a counter, and
+ * a tile waits until every tile of the previous pass of its state has finished
+ * (per-state counters in device memory).  Every such wait is bounded in time
+ * (ts_batch_set_wait; 2 s by default); when one runs out the launch ends early
+ * and the next ts_batch_status, ts_batch_observe, ts_batch_get_states (to host)
+ * or ts_batch_step returns TS_ERR_TIMEOUT.  The launch and the resets of its
+ * counters are captured into one CUDA graph, replayed until tau or nsteps change.
  */
 typedef struct ts_batch ts_batch;
 
@@ -380,14 +385,28 @@ TS4_API ts_status ts_batch_get_schedule(const ts_batch *b, int *tile_bits, int *
  */
 TS4_API ts_status ts_batch_autotune(ts_batch *b, double tau, int reps, const char *cache_path, double *best_ms);
 
-/* nsteps TS4 steps of length tau for every state: one CUDA graph launch (Sec. 2). */
+/* nsteps TS4 steps of length tau for every state: one CUDA graph launch holding one
+ * kernel launch (Sec. 2).  Asynchronous.  Errors: TS_ERR_ARG, TS_ERR_STATE (a system
+ * has no states), TS_ERR_TIMEOUT (an earlier launch gave up; reported once), TS_ERR_CUDA. */
 TS4_API ts_status ts_batch_step(ts_batch *b, double tau, int64_t nsteps);
+
+/* Waits for the batch's queued work.  TS_ERR_TIMEOUT, reported once, if a dependency
+ * wait of a launch ran out since the last report (the states are then undefined until
+ * they are set again); TS_OK otherwise. */
+TS4_API ts_status ts_batch_status(ts_batch *b);
+
+/* Bounds every dependency wait of the ensemble kernel to limit_s seconds (0 < limit_s
+ * <= 60; default 2).  hold != 0 makes every wait also wait for a device flag that
+ * nothing sets, so that each one runs out: a test of the timeout path, which leaves
+ * the device usable (the kernel returns; no fault, no endless wait).
+ * Errors: TS_ERR_ARG. */
+TS4_API ts_status ts_batch_set_wait(ts_batch *b, double limit_s, int hold);
 
 /* TS_NORM (one double per state) or TS_SZ (N[k] doubles per state), systems in
  * order, states in order; synchronises the stream. */
 TS4_API ts_status ts_batch_observe(ts_batch *b, int what, double *out);
 
-/* Kernels launched so far (graph nodes count one each). */
+/* Kernels launched so far (one per ts_batch_step; plus the reductions of ts_batch_observe). */
 TS4_API int64_t ts_batch_kernel_launches(const ts_batch *b);
 
 /* Text of the last error of b (never NULL). */

@@ -1830,9 +1830,11 @@ double ts_step_bound_host(int N, const double *Jx, const double *Jy, const doubl
 
 // ================================================================== batched ensemble
 //
-// Many states of several systems (uneven N) advance together: at every pass
-// index one k_tile_batch launch covers every state of every system, and the
-// whole ts_batch_step is captured into one CUDA graph and replayed.
+// Many states of several systems (uneven N) advance together: one launch of the
+// persistent kernel k_tile_ensemble runs every pass of every state of a
+// ts_batch_step (per-state completion counters order the passes of a state), and
+// that launch, with the resets of its counters, is captured into one CUDA graph
+// and replayed.
 
 struct ts_batch {
     int nsys = 0;
@@ -1847,7 +1849,17 @@ struct ts_batch {
     BatchSys *dsys = nullptr;
     TileArgs *dargs = nullptr;
     size_t dcap = 0;                 // entries
-    std::vector<uint64_t> blocks;    // blocks per pass index
+    std::vector<uint64_t> blocks;    // work items (chunks of tiles) per pass index
+    uint64_t *dpstart = nullptr;     // first work item of each pass (npass + 1)
+    size_t pstart_cap = 0;           // entries
+    // synchronisation words of the persistent kernel: ticket, per-state counters, status
+    unsigned long long *dsync = nullptr;
+    size_t sync_cap = 0;             // counters (ticket + states)
+    int *dstatus = nullptr;          // [0] sticky status, [1] the word nothing writes
+    int *hstatus = nullptr;          // pinned copy of the status after each launch
+    double wait_limit_s = 2.0;       // longest dependency wait of a launch
+    int hold = 0;                    // test of the timeout path
+    unsigned grid = 0;               // persistent blocks: SMs x resident blocks per SM
     // cached graph of the last (tau, nsteps)
     cudaGraphExec_t gexec = nullptr;
     double g_tau = 0.0;
@@ -1877,40 +1889,53 @@ ts_status bfail(ts_batch *b, ts_status st, const std::string &msg)
                          std::string(#call) + ": " + cudaGetErrorString(e_));                     \
     } while (0)
 
+// Tiles per work item of the persistent ensemble kernel: 2^3 (fewer ticket atomics and
+// counter updates per tile; a state's pass always splits into whole items).
+constexpr int kEnsembleChunkShift = 3;
+
 size_t batch_state_bytes(const ts_batch *b, int s)
 {
     return (size_t)b->nstates[s] * state_bytes(b->sys[s]);
 }
 
 template <typename R, int TB, int RB>
-cudaError_t launch_batch_t(cudaStream_t st, const BatchSys *sys, const TileArgs *args, int nsys, uint64_t nblk)
+cudaError_t launch_batch_t(const ts_batch *b, const BatchSync &sy, bool attr, unsigned *grid)
 {
     using K = TileKernel<R, TB, RB>;
     constexpr size_t smem = sizeof(typename CT<R>::T) * K::SMEM_ELEMS;
-    k_tile_batch<R, TB, RB><<<(unsigned)nblk, K::NT, smem, st>>>(sys, args, nsys);
+    if (attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_ensemble<R, TB, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        int per_sm = 0, dev = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_ensemble<R, TB, RB>, K::NT, smem);
+        if (e == cudaSuccess)
+            e = cudaGetDevice(&dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        *grid = (unsigned)(std::max(per_sm, 1) * std::max(sms, 1));
+        return e;
+    }
+    k_tile_ensemble<R, TB, RB><<<*grid, K::NT, smem, b->stream>>>(b->dsys, b->dargs, b->nsys, sy);
     return cudaGetLastError();
 }
 
-template <typename R, int TB, int RB> cudaError_t batch_attr_t()
+// attr: set the kernel's shared-memory attribute and size the persistent grid; otherwise launch.
+cudaError_t launch_batch(ts_batch *b, const BatchSync &sy, bool attr)
 {
-    using K = TileKernel<R, TB, RB>;
-    constexpr size_t smem = sizeof(typename CT<R>::T) * K::SMEM_ELEMS;
-    return cudaFuncSetAttribute(k_tile_batch<R, TB, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-cudaError_t launch_batch(const ts_batch *b, const BatchSys *sys, const TileArgs *args, uint64_t nblk, bool attr)
-{
+    unsigned *g = &b->grid;
     if (b->prec == TS_C64) {
         switch (b->TB) {
-        case 12: return attr ? batch_attr_t<float, 12, 5>() : launch_batch_t<float, 12, 5>(b->stream, sys, args, b->nsys, nblk);
-        case 13: return attr ? batch_attr_t<float, 13, 5>() : launch_batch_t<float, 13, 5>(b->stream, sys, args, b->nsys, nblk);
-        default: return attr ? batch_attr_t<float, 14, 5>() : launch_batch_t<float, 14, 5>(b->stream, sys, args, b->nsys, nblk);
+        case 12: return launch_batch_t<float, 12, 5>(b, sy, attr, g);
+        case 13: return launch_batch_t<float, 13, 5>(b, sy, attr, g);
+        default: return launch_batch_t<float, 14, 5>(b, sy, attr, g);
         }
     }
     switch (b->TB) {
-    case 11: return attr ? batch_attr_t<double, 11, 4>() : launch_batch_t<double, 11, 4>(b->stream, sys, args, b->nsys, nblk);
-    case 12: return attr ? batch_attr_t<double, 12, 4>() : launch_batch_t<double, 12, 4>(b->stream, sys, args, b->nsys, nblk);
-    default: return attr ? batch_attr_t<double, 13, 4>() : launch_batch_t<double, 13, 4>(b->stream, sys, args, b->nsys, nblk);
+    case 11: return launch_batch_t<double, 11, 4>(b, sy, attr, g);
+    case 12: return launch_batch_t<double, 12, 4>(b, sy, attr, g);
+    default: return launch_batch_t<double, 13, 4>(b, sy, attr, g);
     }
 }
 
@@ -1969,7 +1994,11 @@ ts_status batch_prepare(ts_batch *b, double tau, int64_t n)
             bs.tabs = S.dtab;
             bs.n = c->N;
             bs.tile_shift = c->N - b->TB;
+            bs.chunk_shift = std::min(bs.tile_shift, kEnsembleChunkShift);
             bs.block_start = start;
+            bs.state_base = 0;
+            for (int q = 0; q < s; q++)
+                bs.state_base += (uint32_t)b->nstates[q];
             bs.active = p < S.passes.size();
             if (!bs.active)
                 continue;
@@ -1990,24 +2019,68 @@ ts_status batch_prepare(ts_batch *b, double tau, int64_t n)
             a.theta = hp.slot >= 0 ? S.dtheta + hp.theta_off : nullptr;
             a.gfield = hp.slot >= 0 ? gfield_at(c, S, hp.theta_off) : nullptr;
             set_io_args(a, c, S, hp.group);
-            start += (uint32_t)((uint64_t)b->nstates[s] << bs.tile_shift);
+            start += (uint32_t)((uint64_t)b->nstates[s] << (bs.tile_shift - bs.chunk_shift));
         }
         b->blocks[p] = start;
     }
+    // first work item of every pass, and the synchronisation words
+    std::vector<uint64_t> pst(maxp + 1, 0);
+    for (size_t p = 0; p < maxp; p++)
+        pst[p + 1] = pst[p] + b->blocks[p];
+    if (pst.size() > b->pstart_cap) {
+        if (b->dpstart)
+            cudaFree(b->dpstart);
+        b->dpstart = nullptr;
+        b->pstart_cap = 0;
+        TS_BCUDA(b, cudaMalloc(&b->dpstart, pst.size() * sizeof(uint64_t)));
+        b->pstart_cap = pst.size();
+    }
+    size_t nst = 0;
+    for (int s = 0; s < b->nsys; s++)
+        nst += (size_t)b->nstates[s];
+    if (1 + nst > b->sync_cap) {
+        if (b->dsync)
+            cudaFree(b->dsync);
+        b->dsync = nullptr;
+        b->sync_cap = 0;
+        TS_BCUDA(b, cudaMalloc(&b->dsync, (1 + nst) * sizeof(unsigned long long)));
+        b->sync_cap = 1 + nst;
+    }
+    if (!b->dstatus) {
+        TS_BCUDA(b, cudaMalloc(&b->dstatus, 2 * sizeof(int)));
+        TS_BCUDA(b, cudaMemsetAsync(b->dstatus, 0, 2 * sizeof(int), b->stream));
+    }
+    if (!b->hstatus) {
+        TS_BCUDA(b, cudaHostAlloc(&b->hstatus, sizeof(int), cudaHostAllocDefault));
+        *b->hstatus = 0;
+    }
     TS_BCUDA(b, cudaMemcpyAsync(b->dsys, hs.data(), need * sizeof(BatchSys), cudaMemcpyHostToDevice, b->stream));
     TS_BCUDA(b, cudaMemcpyAsync(b->dargs, ha.data(), need * sizeof(TileArgs), cudaMemcpyHostToDevice, b->stream));
+    TS_BCUDA(b, cudaMemcpyAsync(b->dpstart, pst.data(), pst.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                                b->stream));
     TS_BCUDA(b, cudaStreamSynchronize(b->stream));
-    TS_BCUDA(b, launch_batch(b, nullptr, nullptr, 0, true));
-    // capture the whole evolution into one graph
+    BatchSync sy;
+    sy.ticket = b->dsync;
+    sy.done = b->dsync + 1;
+    sy.status = b->dstatus;
+    sy.hold_flag = b->dstatus + 1;
+    sy.pstart = b->dpstart;
+    sy.limit_ns = (uint64_t)(b->wait_limit_s * 1e9);
+    sy.npass = (int)maxp;
+    sy.hold = b->hold;
+    TS_BCUDA(b, launch_batch(b, sy, true));
+    // capture the whole evolution into one graph: reset the ticket and the per-state counters,
+    // run the persistent kernel, copy the status out
     cudaGraph_t graph = nullptr;
     // (the legacy default stream cannot be captured: record on a private stream)
     TS_BCUDA(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = cudaSuccess;
     const cudaStream_t user = b->stream;
     b->stream = b->cap;
-    for (size_t p = 0; p < maxp && ce == cudaSuccess; p++)
-        if (b->blocks[p])
-            ce = launch_batch(b, b->dsys + p * b->nsys, b->dargs + p * b->nsys, b->blocks[p], false);
+    cudaError_t ce = cudaMemsetAsync(b->dsync, 0, (1 + nst) * sizeof(unsigned long long), b->cap);
+    if (ce == cudaSuccess && pst[maxp] > 0)
+        ce = launch_batch(b, sy, false);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(b->hstatus, b->dstatus, sizeof(int), cudaMemcpyDeviceToHost, b->cap);
     b->stream = user;
     cudaError_t ee = cudaStreamEndCapture(b->cap, &graph);
     if (ce != cudaSuccess || ee != cudaSuccess) {
@@ -2025,7 +2098,23 @@ ts_status batch_prepare(ts_batch *b, double tau, int64_t n)
     }
     b->g_tau = tau;
     b->g_n = n;
-    b->g_nodes = (int64_t)nodes;
+    b->g_nodes = pst[maxp] > 0 ? 1 : 0;   // kernel launches per replay (the other nodes are copies)
+    (void)nodes;
+    return TS_OK;
+}
+
+// Waits for the batch's queued work; TS_ERR_TIMEOUT (once) if a dependency wait of the
+// persistent kernel ran out since the last check.
+ts_status batch_check(ts_batch *b)
+{
+    TS_BCUDA(b, cudaStreamSynchronize(b->stream));
+    if (b->hstatus && *b->hstatus) {
+        *b->hstatus = 0;
+        TS_BCUDA(b, cudaMemsetAsync(b->dstatus, 0, sizeof(int), b->stream));
+        TS_BCUDA(b, cudaStreamSynchronize(b->stream));
+        return bfail(b, TS_ERR_TIMEOUT, "ts_batch_step: a dependency wait of the ensemble kernel ran out; the "
+                                        "states are undefined until they are set again");
+    }
     return TS_OK;
 }
 
@@ -2133,7 +2222,7 @@ ts_status ts_batch_get_states(ts_batch *b, int sys, void *amps, int on_device)
     TS_BCUDA(b, cudaMemcpyAsync(amps, b->psi[sys].p, batch_state_bytes(b, sys),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
     if (!on_device)
-        TS_BCUDA(b, cudaStreamSynchronize(b->stream));
+        return batch_check(b);
     return TS_OK;
 }
 
@@ -2170,6 +2259,8 @@ ts_status ts_batch_step(ts_batch *b, double tau, int64_t nsteps)
             return bfail(b, TS_ERR_STATE, "ts_batch_step: a system has no states set");
     if (nsteps == 0)
         return TS_OK;
+    if (b->hstatus && *b->hstatus)   // an earlier launch gave up: report it before more work
+        return batch_check(b);
     if (!b->gexec || b->g_tau != tau || b->g_n != nsteps) {
         ts_status st = batch_prepare(b, tau, nsteps);
         if (st)
@@ -2180,12 +2271,36 @@ ts_status ts_batch_step(ts_batch *b, double tau, int64_t nsteps)
     return TS_OK;
 }
 
+ts_status ts_batch_status(ts_batch *b)
+{
+    if (!b)
+        return TS_ERR_ARG;
+    return batch_check(b);
+}
+
+ts_status ts_batch_set_wait(ts_batch *b, double limit_s, int hold)
+{
+    if (!b)
+        return TS_ERR_ARG;
+    if (!(limit_s > 0.0) || !std::isfinite(limit_s) || limit_s > 60.0)
+        return bfail(b, TS_ERR_ARG, "ts_batch_set_wait: the limit must be in (0, 60] seconds");
+    b->wait_limit_s = limit_s;
+    b->hold = hold != 0;
+    batch_drop_graph(b);
+    return TS_OK;
+}
+
 ts_status ts_batch_observe(ts_batch *b, int what, double *out)
 {
     if (!b || !out)
         return b ? bfail(b, TS_ERR_ARG, "ts_batch_observe: NULL output") : TS_ERR_ARG;
     if (what != TS_NORM && what != TS_SZ)
         return bfail(b, TS_ERR_ARG, "ts_batch_observe: only TS_NORM and TS_SZ are batched");
+    {
+        const ts_status cs = batch_check(b);
+        if (cs)
+            return cs;
+    }
     size_t o = 0;
     for (int s = 0; s < b->nsys; s++) {
         ts_ctx *c = b->sys[s];
@@ -2226,6 +2341,14 @@ ts_status ts_batch_destroy(ts_batch *b)
         cudaFree(b->dsys);
     if (b->dargs)
         cudaFree(b->dargs);
+    if (b->dpstart)
+        cudaFree(b->dpstart);
+    if (b->dsync)
+        cudaFree(b->dsync);
+    if (b->dstatus)
+        cudaFree(b->dstatus);
+    if (b->hstatus)
+        cudaFreeHost(b->hstatus);
     if (b->hout)
         cudaFreeHost(b->hout);
     if (b->cap)
@@ -2464,6 +2587,8 @@ ts_status ts_batch_autotune(ts_batch *b, double tau, int reps, const char *cache
     }
     if (re == cudaSuccess)
         re = cudaStreamSynchronize(b->stream);
+    if (re == cudaSuccess && !st)
+        st = batch_check(b);
     cudaFree(save);
     if (e0)
         cudaEventDestroy(e0);

@@ -499,11 +499,21 @@ template <typename R, int TB, int RB> struct TileKernel {
                 gi |= gst[b];
         return gi;
     }
-    template <int... J>
+    // loads of the tile: streaming (__ldcs), or through L2 only (__ldcg) when the data were
+    // written by other thread blocks of the same launch (the persistent ensemble kernel), so
+    // that no stale L1 line can be hit
+    template <bool CG> static __device__ __forceinline__ C ld_amp(const C *p)
+    {
+        if constexpr (CG)
+            return __ldcg(p);
+        else
+            return __ldcs(p);
+    }
+    template <bool CG, int... J>
     static __device__ __forceinline__ void gload(const C *__restrict__ psi, uint64_t gthr, const uint64_t (&gst)[RB],
                                                  C (&x)[NR], std::integer_sequence<int, J...>)
     {
-        ((x[J] = __ldcs(psi + gidx<J>(gthr, gst))), ...);
+        ((x[J] = ld_amp<CG>(psi + gidx<J>(gthr, gst))), ...);
     }
     template <int... J>
     static __device__ __forceinline__ void gstore(C *__restrict__ psi, uint64_t gthr, const uint64_t (&gst)[RB],
@@ -522,11 +532,11 @@ template <typename R, int TB, int RB> struct TileKernel {
                 o += gst[b];
         return o;
     }
-    template <int... J>
+    template <bool CG, int... J>
     static __device__ __forceinline__ void gload32(const C *__restrict__ p, const uint32_t (&gst)[RB], C (&x)[NR],
                                                    std::integer_sequence<int, J...>)
     {
-        ((x[J] = __ldcs(p + goff32<J>(gst))), ...);
+        ((x[J] = ld_amp<CG>(p + goff32<J>(gst))), ...);
     }
     template <int... J>
     static __device__ __forceinline__ void gstore32(C *__restrict__ p, const uint32_t (&gst)[RB], const C (&x)[NR],
@@ -555,7 +565,8 @@ template <typename R, int TB, int RB> struct TileKernel {
 // One tile f of the state psi through the pass described by a.
 // SLOT = false compiles a pass without a slot (the middle passes): no slot tables, no
 // per-thread factors in shared memory, fewer registers, so more blocks per SM.
-template <typename R, int TB, int RB, bool SLOT>
+// CG = true loads the tile through L2 only (see ld_amp).
+template <typename R, int TB, int RB, bool SLOT, bool CG = false>
 __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, const TileArgs &a,
                                           const TileTab<R, TB, RB> *__restrict__ tabs, uint64_t f)
 {
@@ -620,9 +631,9 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
         gst32[b] = (uint32_t)gst[b];
     C x[NR];
     if (narrow)
-        K::gload32(psi + gthr, gst32, x, std::make_integer_sequence<int, NR>{});
+        K::template gload32<CG>(psi + gthr, gst32, x, std::make_integer_sequence<int, NR>{});
     else
-        K::gload(psi, gthr, gst, x, std::make_integer_sequence<int, NR>{});
+        K::template gload<CG>(psi, gthr, gst, x, std::make_integer_sequence<int, NR>{});
 
     // ---- per-block part of the slot into shared memory
     int pcq = 0;
@@ -754,34 +765,139 @@ k_tile(typename CT<R>::T *__restrict__ psi, const __grid_constant__ TileArgs a,
     tile_pass<R, TB, RB, SLOT>(psi, a, tabs, blockIdx.x);
 }
 
-// Ensemble pass: every state of every system of a batch through its own pass
-// (one system's arguments per entry of `args`).  Blocks are laid out system by
-// system, state by state, tile by tile: block_start[s] is the first block of
-// system s, and system s has 2^tile_shift[s] tiles per state of 2^n[s] amplitudes.
+// Persistent ensemble kernel: every pass of every state of every system of a batch in one
+// launch (the typical-state ensembles of App. A).
+//
+// Work items are chunks of up to 2^chunk_shift tiles of one state in one pass, in pass-major
+// order: all items of pass p of every state come before any item of pass p + 1.  A block takes
+// the next item from a global ticket counter (it fetches its following ticket as soon as it
+// starts an item, so that the atomic's latency hides behind the item's tiles).  A tile of pass
+// p reads amplitudes that every tile of pass p - 1 of its state wrote (the passes rotate
+// different bit groups), so an item first waits until its state's counter of completed tiles
+// reaches p x (tiles per pass); after its tiles the block adds their number.  A block only
+// waits for items with smaller tickets, and the smallest unfinished ticket is always held by a
+// block that is working on it (a block holding a fetched-ahead ticket is still working on a
+// smaller one), so the launch always progresses, whatever the number of resident blocks.
+// Every wait is bounded in time (%globaltimer): when it runs out, the block sets the sticky
+// status word and returns, and every other block returns before its next item, so the launch
+// ends and the host reports TS_ERR_TIMEOUT.
 struct BatchSys {
     void *psi;           // nstates x 2^n amplitudes
     const void *tabs;    // this system's per-slot tables
     int n;
     int tile_shift;      // log2 tiles per state
-    uint32_t block_start;
+    int chunk_shift;     // log2 tiles per work item (<= tile_shift)
+    uint32_t block_start; // first work item of this system within its pass
+    uint32_t state_base;  // index of the system's first state among all states of the batch
     int active;          // 0: this system has no pass at this index
 };
 
+struct BatchSync {
+    unsigned long long *ticket;   // next work item (zero at launch)
+    unsigned long long *done;     // per state: tiles completed, over all passes (zero at launch)
+    int *status;                  // sticky: nonzero after a dependency wait ran out
+    const int *hold_flag;         // a device word that nothing writes (test of the timeout path)
+    const uint64_t *pstart;       // first work item of each pass; pstart[npass] = all items
+    uint64_t limit_ns;            // longest dependency wait
+    int npass;
+    int hold;                     // nonzero: every wait also waits for *hold_flag (never set)
+};
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits until *cnt >= need (and, with sy.hold, for the flag nothing sets).  Bounded: gives up
+// after sy.limit_ns nanoseconds or 2^26 polls, or as soon as another block gave up.
+__device__ __forceinline__ bool wait_count(const unsigned long long *cnt, unsigned long long need, const BatchSync &sy)
+{
+    const uint64_t t0 = global_ns();
+    unsigned sleep_ns = 32;
+    for (uint32_t it = 0; it < (1u << 26); it++) {
+        const unsigned long long v = *(volatile const unsigned long long *)cnt;
+        if (v >= need && !(sy.hold && *(volatile const int *)sy.hold_flag == 0)) {
+            __threadfence();   // acquire: the counted tiles' stores are visible from here on
+            return true;
+        }
+        if (*(volatile const int *)sy.status != 0)
+            return false;
+        if (global_ns() - t0 > sy.limit_ns)
+            break;
+        __nanosleep(sleep_ns);
+        if (sleep_ns < 2048)
+            sleep_ns *= 2;
+    }
+    atomicExch(sy.status, 1);
+    return false;
+}
+
 template <typename R, int TB, int RB>
 __global__ void __launch_bounds__(1 << (TB - RB), tile_min_blocks(TB - RB, (int)(sizeof(typename CT<R>::T) / 4) << RB))
-k_tile_batch(const BatchSys *__restrict__ sys, const TileArgs *__restrict__ args, int nsys)
+k_tile_ensemble(const BatchSys *__restrict__ sys, const TileArgs *__restrict__ args, int nsys, const BatchSync sy)
 {
-    const uint32_t b = blockIdx.x;
-    int s = 0;
-    while (s + 1 < nsys && sys[s + 1].block_start <= b)
-        s++;
-    if (!sys[s].active)
-        return;
-    const uint32_t local = b - sys[s].block_start;
-    const uint32_t state = local >> sys[s].tile_shift;
-    const uint64_t f = local & ((1u << sys[s].tile_shift) - 1u);
-    typename CT<R>::T *psi = reinterpret_cast<typename CT<R>::T *>(sys[s].psi) + ((uint64_t)state << sys[s].n);
-    tile_pass<R, TB, RB, true>(psi, args[s], reinterpret_cast<const TileTab<R, TB, RB> *>(sys[s].tabs), f);
+    __shared__ int w_go, w_pass, w_sys, w_ntiles;
+    __shared__ uint32_t w_state;
+    __shared__ uint64_t w_tile0;
+    const uint64_t total = sy.pstart[sy.npass];
+    unsigned long long next = 0;   // thread 0: the ticket fetched ahead
+    int pass_hint = 0;             // thread 0: tickets only grow, so the pass search starts here
+    if (threadIdx.x == 0)
+        next = atomicAdd(sy.ticket, 1ull);
+    for (;;) {
+        __syncthreads();   // the previous item's shared-memory reads are done
+        if (threadIdx.x == 0) {
+            int go = 0;
+            const unsigned long long t = next;
+            if (t < total && *(volatile const int *)sy.status == 0) {
+                next = atomicAdd(sy.ticket, 1ull);
+                int p = pass_hint;
+                while (p + 1 < sy.npass && sy.pstart[p + 1] <= t)
+                    p++;
+                pass_hint = p;
+                const BatchSys *row = sys + (size_t)p * nsys;
+                const uint32_t local = (uint32_t)(t - sy.pstart[p]);
+                int s = 0;
+                while (s + 1 < nsys && row[s + 1].block_start <= local)
+                    s++;
+                if (row[s].active) {
+                    const int per_state = row[s].tile_shift - row[s].chunk_shift;   // log2 items per state
+                    const uint32_t li = local - row[s].block_start;
+                    const uint32_t state = li >> per_state;
+                    w_pass = p;
+                    w_sys = s;
+                    w_state = state;
+                    w_tile0 = (uint64_t)(li & ((1u << per_state) - 1u)) << row[s].chunk_shift;
+                    w_ntiles = 1 << row[s].chunk_shift;
+                    const unsigned long long need = (unsigned long long)p << row[s].tile_shift;
+                    go = wait_count(sy.done + row[s].state_base + state, need, sy) ? 1 : 0;
+                }
+            }
+            w_go = go;
+        }
+        __syncthreads();
+        if (!w_go)
+            return;
+        const int p = w_pass, s = w_sys, nt = w_ntiles;
+        const uint32_t state = w_state;
+        const uint64_t f0 = w_tile0;
+        const BatchSys &bs = sys[(size_t)p * nsys + s];
+        typename CT<R>::T *psi = reinterpret_cast<typename CT<R>::T *>(bs.psi) + ((uint64_t)state << bs.n);
+        const TileArgs &a = args[(size_t)p * nsys + s];
+        const TileTab<R, TB, RB> *tabs = reinterpret_cast<const TileTab<R, TB, RB> *>(bs.tabs);
+        for (int k = 0; k < nt; k++) {
+            if (k)
+                __syncthreads();   // the previous tile's shared-memory reads are done
+            tile_pass<R, TB, RB, true, true>(psi, a, tabs, f0 + k);
+        }
+        __syncthreads();   // every thread's stores come before thread 0's fence and count
+        if (threadIdx.x == 0) {
+            __threadfence();   // release (cumulative over the block's stores seen at the barrier)
+            atomicAdd(sy.done + bs.state_base + state, (unsigned long long)nt);
+        }
+    }
 }
 
 } // namespace ts4

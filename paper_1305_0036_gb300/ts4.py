@@ -62,6 +62,8 @@ SIGNATURES = {
     "ts_batch_get_schedule": (_I, [_P, _P, _P]),
     "ts_batch_autotune": (_I, [_P, _D, _I, ctypes.c_char_p, _P]),
     "ts_batch_step": (_I, [_P, _D, _I64]),
+    "ts_batch_status": (_I, [_P]),
+    "ts_batch_set_wait": (_I, [_P, _D, _I]),
     "ts_batch_observe": (_I, [_P, _I, _P]),
     "ts_batch_kernel_launches": (_I64, [_P]),
     "ts_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -312,6 +314,14 @@ class Batch:
 
     def step(self, tau, nsteps=1):
         _bcheck(_lib.ts_batch_step(self.b, float(tau), int(nsteps)), self.b)
+
+    def status(self):
+        """Waits for the queued work; raises TS4Error(TS_ERR_TIMEOUT) if a dependency wait ran out."""
+        _bcheck(_lib.ts_batch_status(self.b), self.b)
+
+    def set_wait(self, limit_s=2.0, hold=False):
+        """Bound of every dependency wait of the ensemble kernel; hold=True tests the timeout path."""
+        _bcheck(_lib.ts_batch_set_wait(self.b, float(limit_s), 1 if hold else 0), self.b)
 
     def norms(self):
         out = np.zeros(sum(self.nstates))

@@ -1,5 +1,6 @@
 """Batched ensemble (several systems of uneven N, many states each) against the
-oracle and against single-state runs of the same library."""
+oracle and against single-state runs of the same library; the persistent ensemble
+kernel's one launch per step and its bounded dependency waits."""
 import numpy as np
 import pytest
 
@@ -39,9 +40,66 @@ def test_small_batch_matches_oracle(ts4, prec):
                 assert np.linalg.norm(got[j] - ref) <= 20 * nsteps * (s.N + 8) * U32
     norms = b.norms()
     assert np.all(np.abs(norms - 1) <= (1e-12 if prec == "c128" else 1e-5))
-    # a second call replays the cached graph
+    # a second call replays the cached graph: one persistent kernel launch per step call
+    l0 = b.launches()
     b.step(tau, nsteps)
-    assert b.launches() > 0
+    b.status()
+    assert b.launches() - l0 == 1
+    b.close()
+
+
+def test_ensemble_many_steps_uneven_passes_match_oracle(ts4):
+    """Systems with 1, 2 and 3 bit groups (different numbers of passes per step: 20, 20, 40)
+    over 12 steps, so that the per-state counters order thousands of dependent tiles."""
+    systems = [W.xyz_chain(12, 1.0, 0.8, 0.5, seed=41), W.random_system(16, 42, transverse=False),
+               W.xyz_chain(21, 1.0, 0.8, 0.5, seed=43)]
+    nst = [5, 3, 1]
+    b = ts4.Batch(systems, nst, prec="c128")
+    b.set_schedule(12, 4)
+    init = []
+    for i, (s, k) in enumerate(zip(systems, nst)):
+        a = np.stack([W.haar_state(s.N, 2000 + 10 * i + j) for j in range(k)])
+        init.append(a)
+        b.set_states(i, a)
+    nsteps, tau = 12, 0.04
+    b.step(tau, nsteps)
+    for i, (s, k) in enumerate(zip(systems, nst)):
+        got = b.get_states(i)
+        for j in sorted({0, k - 1}):
+            ref = oracle.ts4(init[i][j], _ham(s), tau, nsteps)
+            assert np.abs(got[j] - ref).max() <= 1e-12, (i, j)
+    b.close()
+
+
+def test_ensemble_wait_timeout_is_reported_and_recoverable(ts4):
+    """Every dependency wait made to run out (a device flag that nothing sets): the launch
+    ends by itself, the timeout is reported once, and the batch works again afterwards."""
+    systems = [W.xyz_chain(12, 1.0, 0.8, 0.5, seed=51), W.xyz_chain(14, 1.0, 0.8, 0.5, seed=52)]
+    nst = [2, 2]
+    b = ts4.Batch(systems, nst, prec="c64")
+    b.set_schedule(12, 2)
+    init = [np.stack([W.haar_state(s.N, 3000 + 10 * i + j, np.complex64) for j in range(k)])
+            for i, (s, k) in enumerate(zip(systems, nst))]
+    for i in range(2):
+        b.set_states(i, init[i])
+    b.set_wait(0.05, hold=True)
+    b.step(0.05, 2)
+    with pytest.raises(ts4.TS4Error) as e:
+        b.status()
+    assert e.value.status == ts4.TS_ERR_TIMEOUT
+    b.status()                      # reported once
+    b.set_wait(2.0, hold=False)
+    for i in range(2):
+        b.set_states(i, init[i])
+    b.step(0.05, 2)
+    for i, (s, k) in enumerate(zip(systems, nst)):
+        got = b.get_states(i).astype(np.complex128)
+        for j in range(k):
+            ref = oracle.ts4(init[i][j].astype(np.complex128), _ham(s), 0.05, 2)
+            assert np.linalg.norm(got[j] - ref) <= 40 * (s.N + 8) * U32
+    with pytest.raises(ts4.TS4Error) as e:
+        b.set_wait(0.0)
+    assert e.value.status == ts4.TS_ERR_ARG
     b.close()
 
 
