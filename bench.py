@@ -330,6 +330,36 @@ def config4_ensemble(ts4, torch, dev, steps):
     return out
 
 
+def config2_ladder(ts4, torch, dev):
+    """Config 2: the 2x12 ladder (J^a_ij i.i.d. U[-1, 1], h i.i.d. U[-1/2, 1/2]), Neel state,
+    tau = 0.02, 1000 steps: complex64 timed over one ts_step(tau, 1000) call, against the same
+    run in complex128 (S^z and norm drift; targets 1e-5)."""
+    from paper_1305_0036_gb300 import workloads as W
+    cfg = W.config(1)
+    s = cfg["system"]
+    out = {"workload": "N=24 two-leg ladder 2x12, J^a~U[-1,1], h~U[-0.5,0.5], Neel state, tau=0.02, "
+                       "1000 steps, complex64 vs complex128", "steps": cfg["nsteps"]}
+    res = {}
+    for prec in ("c64", "c128"):
+        c = ts4.Context.from_system(s, prec=prec, device=dev)
+        c.set_basis_state(cfg["state"][1])
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(c.stream)
+        c.step(cfg["tau"], cfg["nsteps"])
+        e1.record(c.stream)
+        torch.cuda.synchronize(dev)
+        res[prec] = (e0.elapsed_time(e1) / cfg["nsteps"], c.norm(), c.sz())
+        c.close()
+    out["ms_per_step_c64"] = res["c64"][0]
+    out["ms_per_step_c128"] = res["c128"][0]
+    out["norm_drift_c64"] = abs(res["c64"][1] - 1.0)
+    out["norm_drift_c128"] = abs(res["c128"][1] - 1.0)
+    out["max_abs_dSz"] = float(abs(res["c64"][2] - res["c128"][2]).max())
+    out["targets"] = {"max_abs_dSz": 1e-5, "norm_drift_c64": 1e-5}
+    return out
+
+
 def config5_capacity(ts4, torch, dev, steps):
     """Config 5: N=33 XYZ chain (1.0, 0.8, 0.5), h=0.1, Neel state, tau=0.02, complex64 (64 GiB
     state in place); ms per TS4 step over one ts_step(tau, steps) call."""
@@ -515,6 +545,8 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_oracle_check:
         line["err_vs_oracle"] = oracle_cross_check(ts4)
     if not args.no_configs and N == 28:
+        line["config2"] = config2_ladder(ts4, torch, dev)
+        torch.cuda.empty_cache()
         line["config4"] = config4_ensemble(ts4, torch, dev, 20)
         torch.cuda.empty_cache()
         line["config5"] = config5_capacity(ts4, torch, dev, 2)

@@ -118,6 +118,15 @@ def test_config4_ensemble_against_single_state_runs(ts4):
     norms = b.norms()
     assert np.all(np.abs(norms - 1) <= 1e-4), np.abs(norms - 1).max()
     szs = b.sz()
+    # the two smallest systems' first states against the FP64 oracle after the whole run
+    for i in (0, 1):
+        s = systems[i]
+        got = b.get_states(i)[0].astype(np.complex128)
+        ref = oracle.ts4(init[i][0].astype(np.complex128), _ham(s), cfg["tau"], cfg["nsteps"])
+        L = 20 * cfg["nsteps"] + 1
+        assert np.linalg.norm(got - ref) <= L * (s.N + 8) * U32
+        assert np.abs(got - ref).max() <= np.sqrt(2 * np.log(2.0 ** (s.N + 1))) * L * (s.N + 8) * U32 * np.abs(ref).max()
+        np.testing.assert_allclose(szs[i][0], oracle.sz(ref, s.N), atol=2 * L * (s.N + 8) * U32)
     for i, s in enumerate(systems):
         got = b.get_states(i)
         for j in (0, k - 1):
