@@ -887,10 +887,20 @@ k_tile_ensemble(const BatchSys *__restrict__ sys, const TileArgs *__restrict__ a
         typename CT<R>::T *psi = reinterpret_cast<typename CT<R>::T *>(bs.psi) + ((uint64_t)state << bs.n);
         const TileArgs &a = args[(size_t)p * nsys + s];
         const TileTab<R, TB, RB> *tabs = reinterpret_cast<const TileTab<R, TB, RB> *>(bs.tabs);
-        for (int k = 0; k < nt; k++) {
-            if (k)
-                __syncthreads();   // the previous tile's shared-memory reads are done
-            tile_pass<R, TB, RB, true, true>(psi, a, tabs, f0 + k);
+        // a pass without a slot (the middle passes of three or more bit groups) runs the code
+        // path compiled without the slot machinery, as ts_step's separate kernel build does
+        if (a.has_slot) {
+            for (int k = 0; k < nt; k++) {
+                if (k)
+                    __syncthreads();   // the previous tile's shared-memory reads are done
+                tile_pass<R, TB, RB, true, true>(psi, a, tabs, f0 + k);
+            }
+        } else {
+            for (int k = 0; k < nt; k++) {
+                if (k)
+                    __syncthreads();
+                tile_pass<R, TB, RB, false, true>(psi, a, tabs, f0 + k);
+            }
         }
         __syncthreads();   // every thread's stores come before thread 0's fence and count
         if (threadIdx.x == 0) {
