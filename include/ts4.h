@@ -396,7 +396,7 @@ TS4_API ts_status ts_batch_step(ts_batch *b, double tau, int64_t nsteps);
 TS4_API ts_status ts_batch_status(ts_batch *b);
 
 /* Bounds every dependency wait of the ensemble kernel to limit_s seconds (0 < limit_s
- * <= 60; default 2).  hold != 0 makes every wait also wait for a device flag that
+ * <= 8; default 2; a wait also gives up after 2^22 polls).  hold != 0 makes every wait also wait for a device flag that
  * nothing sets, so that each one runs out: a test of the timeout path, which leaves
  * the device usable (the kernel returns; no fault, no endless wait).
  * Errors: TS_ERR_ARG. */

@@ -2282,8 +2282,8 @@ ts_status ts_batch_set_wait(ts_batch *b, double limit_s, int hold)
 {
     if (!b)
         return TS_ERR_ARG;
-    if (!(limit_s > 0.0) || !std::isfinite(limit_s) || limit_s > 60.0)
-        return bfail(b, TS_ERR_ARG, "ts_batch_set_wait: the limit must be in (0, 60] seconds");
+    if (!(limit_s > 0.0) || !std::isfinite(limit_s) || limit_s > 8.0)
+        return bfail(b, TS_ERR_ARG, "ts_batch_set_wait: the limit must be in (0, 8] seconds");
     b->wait_limit_s = limit_s;
     b->hold = hold != 0;
     batch_drop_graph(b);

@@ -811,12 +811,13 @@ __device__ __forceinline__ uint64_t global_ns()
 }
 
 // Waits until *cnt >= need (and, with sy.hold, for the flag nothing sets).  Bounded: gives up
-// after sy.limit_ns nanoseconds or 2^26 polls, or as soon as another block gave up.
+// after sy.limit_ns nanoseconds or 2^22 polls (at most ~9 s with the 2 us back-off), or as
+// soon as another block gave up.
 __device__ __forceinline__ bool wait_count(const unsigned long long *cnt, unsigned long long need, const BatchSync &sy)
 {
     const uint64_t t0 = global_ns();
     unsigned sleep_ns = 32;
-    for (uint32_t it = 0; it < (1u << 26); it++) {
+    for (uint32_t it = 0; it < (1u << 22); it++) {
         const unsigned long long v = *(volatile const unsigned long long *)cnt;
         if (v >= need && !(sy.hold && *(volatile const int *)sy.hold_flag == 0)) {
             __threadfence();   // acquire: the counted tiles' stores are visible from here on
