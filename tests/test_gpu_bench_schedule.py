@@ -144,3 +144,29 @@ def test_bench_window_geometry_n27_c64_matches_oracle(ts4):
           f"max|dpsi| = {el:.3e} (bound {el_bound:.3e})")
     assert l2 <= l2_bound, l2
     assert el <= el_bound, el
+
+
+def test_bench_instance_n28_one_step_matches_oracle(ts4):
+    """The benchmark's own instance at full size: N=28 dipolar chain, Eq. A.1 state, tau = 0.01,
+    the default complex64 schedule (12-bit tiles, 3 coalescing spins, windows of 8 spins plus
+    the 4 lowest), one TS4 step (41 passes: every pass kind of the timed run) against one FP64
+    oracle step (about three minutes on 16 cores, 8 GiB of host memory)."""
+    N = 28
+    s = W.dipolar_chain(N)
+    psi0 = W.random_phase_state(N, W.SEED_BASE + 3, np.complex64)
+    groups = _check_plan(ts4, N, "c64", 0, 0, 1)
+    assert groups[1] == dict(c=4, w=12, h=8) and groups[2] == dict(c=4, w=20, h=8)
+    ctx = ts4.Context.from_system(s, prec="c64")
+    ctx.set_state(psi0)
+    ctx.step(0.01, 1)
+    got = ctx.get_state()
+    ctx.close()
+    ref = oracle.ts4(psi0.astype(np.complex128), _ham(s), 0.01, 1)
+    l2_bound, el_bound = _bounds_c64(N, 21, ref)
+    err = got.astype(np.complex128)
+    err -= ref
+    l2, el = np.linalg.norm(err), np.abs(err).max()
+    print(f"\nc64 dipolar N=28 (bench instance), 1 step: ||dpsi||_2 = {l2:.3e} (bound {l2_bound:.3e}), "
+          f"max|dpsi| = {el:.3e} (bound {el_bound:.3e})")
+    assert l2 <= l2_bound, l2
+    assert el <= el_bound, el
