@@ -199,24 +199,28 @@ bool tile_supported(ts_prec p, int tb)
 int default_tile(ts_prec) { return 12; }  // fastest at N=28 on GB300 for both precisions (measured)
 int default_cbits(ts_prec p) { return p == TS_C64 ? 3 : 2; }
 
-template <typename R, int TB, int RB, bool SLOT>
+template <typename R, int TB, int RB, bool SLOT, typename SHAPE = RuntimeShape>
 cudaError_t launch_tile_s(cudaStream_t st, void *psi, const TileArgs &a, const void *tabs, uint64_t nblk)
 {
     using K = TileKernel<R, TB, RB>;
     constexpr size_t smem = sizeof(typename CT<R>::T) * K::SMEM_ELEMS;
-    cudaError_t e = cudaFuncSetAttribute(k_tile<R, TB, RB, SLOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_tile<R, TB, RB, SLOT, SHAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess)
         return e;
-    k_tile<R, TB, RB, SLOT><<<(unsigned)nblk, K::NT, smem, st>>>((typename CT<R>::T *)psi, a,
-                                                                  (const TileTab<R, TB, RB> *)tabs);
+    k_tile<R, TB, RB, SLOT, SHAPE><<<(unsigned)nblk, K::NT, smem, st>>>((typename CT<R>::T *)psi, a,
+                                                                         (const TileTab<R, TB, RB> *)tabs);
     return cudaGetLastError();
 }
 
-// Passes without a slot run the kernel compiled without the slot machinery.
+// Passes whose shape is compiled (ts4_shapes_*.cu) run that build; the others follow their step
+// list at run time.  Passes without a slot run a kernel compiled without the slot machinery.
 template <typename R, int TB, int RB>
 cudaError_t launch_tile_t(cudaStream_t st, void *psi, const TileArgs &a, const void *tabs, uint64_t nblk)
 {
+    cudaError_t e = cudaSuccess;
+    if (launch_shaped<R, TB, RB>(st, psi, a, tabs, nblk, &e))
+        return e;
     return a.has_slot ? launch_tile_s<R, TB, RB, true>(st, psi, a, tabs, nblk)
                       : launch_tile_s<R, TB, RB, false>(st, psi, a, tabs, nblk);
 }

@@ -452,6 +452,42 @@ __device__ __forceinline__ void slot_c128(double2 (&x)[16], const SlotSoA128<NT>
     slot_c128_seq(x, o, t, Q, std::make_integer_sequence<int, 16>{});
 }
 
+// ---- compile-time pass shapes
+// A pass is a list of steps: in chunk layout K, rotate the register bits [R0LO, R0HI), apply the
+// slot if PH, rotate [R1LO, R1HI) (the run-time StepDesc).  The shapes of the passes that make up
+// almost all of a long run are also compiled as template lists: the step loop, the chunk
+// switches and the butterfly-range dispatch then vanish, and the compiler schedules across the
+// steps of a pass.  RuntimeShape keeps the run-time loop for every other pass.
+template <int K_, int R0LO_, int R0HI_, int PH_, int R1LO_, int R1HI_> struct Step {
+    static constexpr int K = K_, R0LO = R0LO_, R0HI = R0HI_, PH = PH_, R1LO = R1LO_, R1HI = R1HI_;
+};
+template <int KIO_, typename... S> struct PassShape {
+    static constexpr int KIO = KIO_;
+    static constexpr int NS = (int)sizeof...(S);
+    static constexpr int KPH = (0 + ... + (S::PH ? S::K : 0));   // chunk of the step with the slot
+};
+struct RuntimeShape {};
+
+// Host check: does the pass described by (kio, steps) have shape SH?
+template <int I, typename... S> struct ShapeMatch;
+template <int I> struct ShapeMatch<I> {
+    static bool ok(const StepDesc *) { return true; }
+};
+template <int I, typename S0, typename... S> struct ShapeMatch<I, S0, S...> {
+    static bool ok(const StepDesc *d)
+    {
+        return d[I].k == S0::K && d[I].r0lo == S0::R0LO && d[I].r0hi == S0::R0HI && d[I].ph == S0::PH &&
+               d[I].r1lo == S0::R1LO && d[I].r1hi == S0::R1HI && ShapeMatch<I + 1, S...>::ok(d);
+    }
+};
+template <typename SH> struct ShapeOf;
+template <int KIO, typename... S> struct ShapeOf<PassShape<KIO, S...>> {
+    static bool matches(int kio, int nsteps, const StepDesc *d)
+    {
+        return kio == KIO && nsteps == (int)sizeof...(S) && ShapeMatch<0, S...>::ok(d);
+    }
+};
+
 template <typename R, int TB, int RB> struct TileKernel {
     using C = typename CT<R>::T;
     static constexpr int ES = sizeof(C);
@@ -560,20 +596,78 @@ template <typename R, int TB, int RB> struct TileKernel {
         else
             slot_c128(x, sh.th_f, threadIdx.x, sh.Q);
     }
+    // MODE >= 0: the complex64 factor's series form fixed at compile time
+    template <int MODE>
+    static __device__ __forceinline__ void apply_slot_m(C (&x)[NR], const TileShared<R, TB, RB> &sh, int mode)
+    {
+        if constexpr (sizeof(R) == 4 && MODE >= 0)
+            slot_c64_apply<RB, MODE>(x, sh.th_f, threadIdx.x, sh.Q);
+        else
+            apply_slot(x, sh, mode);
+    }
+
+    // the steps of a compile-time shape (see PassShape), from layout CUR; back to KIO at the end
+    template <int CUR, int KIO, bool SLOT, int MODE, typename BaseOf, typename SH>
+    static __device__ __forceinline__ void run_shape(C (&x)[NR], C *sm, const BaseOf &base_of, const SH &sh, int mode)
+    {
+        if constexpr (CUR != KIO) {
+            __syncthreads();
+            store_chunk<CUR>(sm, padidx<ES>(base_of(CUR)), x);
+            __syncthreads();
+            load_chunk<KIO>(sm, padidx<ES>(base_of(KIO)), x);
+        }
+    }
+    template <int CUR, int KIO, bool SLOT, int MODE, typename BaseOf, typename SH, typename S0, typename... Rest>
+    static __device__ __forceinline__ void run_shape(C (&x)[NR], C *sm, const BaseOf &base_of, const SH &sh, int mode)
+    {
+        if constexpr (S0::K != CUR) {
+            __syncthreads();
+            store_chunk<CUR>(sm, padidx<ES>(base_of(CUR)), x);
+            __syncthreads();
+            load_chunk<S0::K>(sm, padidx<ES>(base_of(S0::K)), x);
+        }
+        wht_fixed<S0::R0LO, S0::R0HI>(x);
+        if constexpr (SLOT && S0::PH)
+            apply_slot_m<MODE>(x, sh, mode);
+        wht_fixed<S0::R1LO, S0::R1HI>(x);
+        run_shape<S0::K, KIO, SLOT, MODE, BaseOf, SH, Rest...>(x, sm, base_of, sh, mode);
+    }
+    template <bool SLOT, int MODE, typename BaseOf, typename SH, int KIO, typename... S>
+    static __device__ __forceinline__ void run_pass_shape(C (&x)[NR], C *sm, const BaseOf &base_of, const SH &sh,
+                                                          int mode, PassShape<KIO, S...>)
+    {
+        run_shape<KIO, KIO, SLOT, MODE, BaseOf, SH, S...>(x, sm, base_of, sh, mode);
+    }
 };
 
 // One tile f of the state psi through the pass described by a.
 // SLOT = false compiles a pass without a slot (the middle passes): no slot tables, no
 // per-thread factors in shared memory, fewer registers, so more blocks per SM.
 // CG = true loads the tile through L2 only (see ld_amp).
-template <typename R, int TB, int RB, bool SLOT, bool CG = false>
+template <typename SH> struct ShapeTraits {
+    static constexpr bool runtime = false;
+    static constexpr int KIO = SH::KIO, KPH = SH::KPH;
+};
+template <> struct ShapeTraits<RuntimeShape> {
+    static constexpr bool runtime = true;
+    static constexpr int KIO = 0, KPH = 0;
+};
+
+// SHAPE: RuntimeShape follows a.steps at run time; a PassShape compiles the pass's steps (the
+// caller launches it only for passes of that shape, which always carry the slot when SLOT).
+// MODE (the complex64 factor's series form, a.exact_sincos) and NARROW (32-bit element offsets,
+// N <= 32) are fixed at compile time when >= 0, read from a otherwise.
+template <typename R, int TB, int RB, bool SLOT, bool CG = false, typename SHAPE = RuntimeShape, int MODE = -1,
+          int NARROW = -1>
 __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, const TileArgs &a,
                                           const TileTab<R, TB, RB> *__restrict__ tabs, uint64_t f)
 {
     using K = TileKernel<R, TB, RB>;
     using C = typename CT<R>::T;
+    using ST = ShapeTraits<SHAPE>;
     constexpr int NR = K::NR, ES = K::ES;
-    const int kio = a.io.chunk;
+    const int kio = ST::runtime ? a.io.chunk : ST::KIO;
+    const bool has_slot = ST::runtime ? (a.has_slot != 0) : SLOT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
     __shared__ typename std::conditional<SLOT, TileShared<R, TB, RB>, char>::type sh_store;
@@ -593,7 +687,7 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
     for (int b = 0; b < RB; b++)
         tc[b] = R(0);
     if constexpr (SLOT) {
-        if (a.has_slot) {
+        if (has_slot) {
             const TileTab<R, TB, RB> *tb = tabs + a.tab;
             if (tid < TB)
                 gv = static_cast<const R *>(a.gfield)[f * TB + tid];
@@ -624,7 +718,7 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
     const uint32_t b3 = (K::NCH > 3) ? K::template chunk_base<3>(tid) : 0u;
     auto base_of = [&](int k) { return k == 0 ? b0 : k == 1 ? b1 : k == 2 ? b2 : b3; };
     // ---- issue the tile's loads first: the slot set-up below runs under their latency
-    const bool narrow = a.ham.N <= 32;   // element offsets of the register window fit in 32 bits
+    const bool narrow = NARROW >= 0 ? (NARROW != 0) : (a.ham.N <= 32);   // element offsets fit in 32 bits
     uint32_t gst32[RB];
 #pragma unroll
     for (int b = 0; b < RB; b++)
@@ -639,9 +733,9 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
     int pcq = 0;
     R scale = R(1);
     float srel = 0.0f;                 // exact scale / rounded scale - 1 (c64: sqrt 1/2 is not exact)
-    const int mode = a.exact_sincos;   // c64 per-amplitude factor: 0 tiny |y|, 1 small |y|, 2 any
+    const int mode = MODE >= 0 ? MODE : a.exact_sincos;   // c64 factor: 0 tiny |y|, 1 small |y|, 2 any
     if constexpr (SLOT) {
-        if (a.has_slot) {
+        if (has_slot) {
             pcq = a.slot.pcq;
             if constexpr (sizeof(R) == 4) {
                 scale = a.slot.scale_f;
@@ -665,11 +759,13 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
 
     // ---- per-thread slot factors, computed before the tile occupies the registers
     if constexpr (SLOT) {
-        if (a.has_slot) {
-            int kph = 0;
-            for (int s = 0; s < a.nsteps; s++)
-                if (a.steps[s].ph)
-                    kph = a.steps[s].k;
+        if (has_slot) {
+            int kph = ST::KPH;
+            if constexpr (ST::runtime) {
+                for (int s = 0; s < a.nsteps; s++)
+                    if (a.steps[s].ph)
+                        kph = a.steps[s].k;
+            }
             if constexpr (sizeof(R) == 4) {
                 SlotThreadC64<RB> o;
                 slot_thread_c64<TB, RB>(o, base_of(kph), kph, sh, pcq, (float)scale, srel, tp, tc);
@@ -683,6 +779,9 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
     }
 
     // ---- steps: transpose to the step's chunk layout when it changes
+    if constexpr (!ST::runtime) {
+        K::template run_pass_shape<SLOT, MODE>(x, sm, base_of, sh, mode, SHAPE{});
+    } else {
     int cur = kio;
     for (int s = 0; s < a.nsteps; s++) {
         const StepDesc d = a.steps[s];
@@ -728,6 +827,7 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
         else
             K::template load_chunk<1>(sm, padidx<ES>(base_io), x);
     }
+    }
 
     // ---- store in the I/O layout
     // (opaque copies: keeps the compiler from holding the 2^RB load addresses live
@@ -757,12 +857,45 @@ __host__ __device__ constexpr int tile_min_blocks(int thread_bits, int reg_elems
     return (65536 / (2 * reg_elems)) >> thread_bits > 0 ? (65536 / (2 * reg_elems)) >> thread_bits : 1;
 }
 
-template <typename R, int TB, int RB, bool SLOT>
+template <typename R, int TB, int RB, bool SLOT, typename SHAPE = RuntimeShape, int MODE = -1, int NARROW = -1>
 __global__ void __launch_bounds__(1 << (TB - RB), tile_min_blocks(TB - RB, (int)(sizeof(typename CT<R>::T) / 4) << RB))
 k_tile(typename CT<R>::T *__restrict__ psi, const __grid_constant__ TileArgs a,
        const TileTab<R, TB, RB> *__restrict__ tabs)
 {
-    tile_pass<R, TB, RB, SLOT>(psi, a, tabs, blockIdx.x);
+    tile_pass<R, TB, RB, SLOT, false, SHAPE, MODE, NARROW>(psi, a, tabs, blockIdx.x);
+}
+
+// Launch of a pass through a compiled shape (ts4_shapes_*.cu): returns false if no compiled
+// shape of this tile matches the pass, else launches it and sets *err.
+template <typename R, int TB, int RB>
+bool launch_shaped(cudaStream_t st, void *psi, const TileArgs &a, const void *tabs, uint64_t nblk, cudaError_t *err)
+{
+    return false;
+}
+template <> bool launch_shaped<float, 12, 5>(cudaStream_t, void *, const TileArgs &, const void *, uint64_t, cudaError_t *);
+template <> bool launch_shaped<double, 12, 4>(cudaStream_t, void *, const TileArgs &, const void *, uint64_t, cudaError_t *);
+
+// One compiled shape: launches k_tile<..., SHAPE, MODE, NARROW> if the pass has that shape, that
+// slot-factor form (MODE, slot passes of complex64 only; -1 = any) and that offset width
+// (NARROW: 1 for N <= 32, 0 above).
+template <typename R, int TB, int RB, bool SLOT, typename SHAPE, int MODE = -1, int NARROW = 1>
+bool launch_if_shape(cudaStream_t st, void *psi, const TileArgs &a, const void *tabs, uint64_t nblk, cudaError_t *err)
+{
+    if ((a.has_slot != 0) != SLOT || !ShapeOf<SHAPE>::matches(a.io.chunk, a.nsteps, a.steps))
+        return false;
+    if ((MODE >= 0 && a.exact_sincos != MODE) || ((a.ham.N <= 32) != (NARROW != 0)))
+        return false;
+    using K = TileKernel<R, TB, RB>;
+    constexpr size_t smem = sizeof(typename CT<R>::T) * K::SMEM_ELEMS;
+    cudaError_t e = cudaFuncSetAttribute(k_tile<R, TB, RB, SLOT, SHAPE, MODE, NARROW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        k_tile<R, TB, RB, SLOT, SHAPE, MODE, NARROW><<<(unsigned)nblk, K::NT, smem, st>>>(
+            (typename CT<R>::T *)psi, a, (const TileTab<R, TB, RB> *)tabs);
+        e = cudaGetLastError();
+    }
+    *err = e;
+    return true;
 }
 
 // Persistent ensemble kernel: every pass of every state of every system of a batch in one

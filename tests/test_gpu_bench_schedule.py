@@ -54,8 +54,10 @@ def _system(kind, N):
 
 
 @functools.lru_cache(maxsize=None)
-def _oracle_run(kind, N, nsteps=NSTEPS):
+def _oracle_run(kind, N, nsteps=NSTEPS, c64_start=False):
     s, psi0, tau = _system(kind, N)
+    if c64_start:      # the initial state as complex64 holds it (what the complex64 runs start from)
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)
     return oracle.ts4(psi0, _ham(s), tau, nsteps)
 
 
@@ -134,7 +136,7 @@ def test_bench_window_geometry_n27_c64_matches_oracle(ts4):
     s, psi0, tau = _system("dipolar", N)
     groups = _check_plan(ts4, N, "c64", 12, 3, n)
     assert groups[1] == dict(c=4, w=12, h=8) and groups[2] == dict(c=5, w=20, h=7)
-    ref = _oracle_run("dipolar", N, n)
+    ref = _oracle_run("dipolar", N, n, c64_start=True)
     got, sched = _run(ts4, s, psi0.astype(np.complex64), tau, "c64", 12, 3, False, n)
     assert (sched["tile_bits"], sched["coalesce_bits"], sched["groups"]) == (12, 3, 3)
     l2_bound, el_bound = _bounds_c64(N, 20 * n + 1, ref)
@@ -144,6 +146,12 @@ def test_bench_window_geometry_n27_c64_matches_oracle(ts4):
           f"max|dpsi| = {el:.3e} (bound {el_bound:.3e})")
     assert l2 <= l2_bound, l2
     assert el <= el_bound, el
+    # complex128 with its default schedule (2 coalescing spins: windows of 8 and 7 spins)
+    got128, sched = _run(ts4, s, psi0.astype(np.complex64).astype(np.complex128), tau, "c128", 0, 0, False, n)
+    assert (sched["tile_bits"], sched["coalesce_bits"], sched["groups"]) == (12, 2, 3)
+    el128 = np.abs(got128 - _oracle_run("dipolar", N, n, c64_start=True)).max()
+    print(f"c128 dipolar N={N}: max|dpsi| = {el128:.3e} (bound 1e-12)")
+    assert el128 <= 1e-12, el128
 
 
 def test_bench_instance_n28_one_step_matches_oracle(ts4):
