@@ -2023,6 +2023,7 @@ ts_status batch_prepare(ts_batch *b, double tau, int64_t n)
             a.theta = hp.slot >= 0 ? S.dtheta + hp.theta_off : nullptr;
             a.gfield = hp.slot >= 0 ? gfield_at(c, S, hp.theta_off) : nullptr;
             set_io_args(a, c, S, hp.group);
+            a.ens_shape = (b->prec == TS_C64 && b->TB == 12) ? ensemble_shape_id(a) : 0;
             start += (uint32_t)((uint64_t)b->nstates[s] << (bs.tile_shift - bs.chunk_shift));
         }
         b->blocks[p] = start;

@@ -93,6 +93,7 @@ struct TileArgs {
     const void *gfield;  // per frame f: g_l(f) for the TB tile spins, R precision  (k_frame_terms)
     const uint4 *iomap;  // per thread of the I/O layout: (global offset lo, hi, local base, 0)
     uint64_t gst[8];     // global offset of each register bit of the I/O layout
+    int ens_shape;       // ensemble kernel: index of the compiled shape of this pass (0 = none)
 };
 
 // The frame-dependent parts of a slot's angle, for every tile f of a geometry
@@ -467,6 +468,9 @@ template <int KIO_, typename... S> struct PassShape {
     static constexpr int KPH = (0 + ... + (S::PH ? S::K : 0));   // chunk of the step with the slot
 };
 struct RuntimeShape {};
+template <typename T> struct TypeTag {
+    using type = T;
+};
 
 // Host check: does the pass described by (kio, steps) have shape SH?
 template <int I, typename... S> struct ShapeMatch;
@@ -657,10 +661,13 @@ template <> struct ShapeTraits<RuntimeShape> {
 // caller launches it only for passes of that shape, which always carry the slot when SLOT).
 // MODE (the complex64 factor's series form, a.exact_sincos) and NARROW (32-bit element offsets,
 // N <= 32) are fixed at compile time when >= 0, read from a otherwise.
+// sh_ext: shared-memory slot state provided by the caller (a kernel that inlines several builds
+// of this function passes one block so that each build does not reserve its own); NULL = own.
 template <typename R, int TB, int RB, bool SLOT, bool CG = false, typename SHAPE = RuntimeShape, int MODE = -1,
-          int NARROW = -1>
+          int NARROW = -1, bool EXT_SH = false>
 __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, const TileArgs &a,
-                                          const TileTab<R, TB, RB> *__restrict__ tabs, uint64_t f)
+                                          const TileTab<R, TB, RB> *__restrict__ tabs, uint64_t f,
+                                          void *sh_ext = nullptr)
 {
     using K = TileKernel<R, TB, RB>;
     using C = typename CT<R>::T;
@@ -670,8 +677,9 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
     const bool has_slot = ST::runtime ? (a.has_slot != 0) : SLOT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
-    __shared__ typename std::conditional<SLOT, TileShared<R, TB, RB>, char>::type sh_store;
-    auto &sh = sh_store;
+    using TSH = typename std::conditional<SLOT, TileShared<R, TB, RB>, char>::type;
+    __shared__ typename std::conditional<EXT_SH, char, TSH>::type sh_store;
+    TSH &sh = EXT_SH ? *reinterpret_cast<TSH *>(sh_ext) : reinterpret_cast<TSH &>(sh_store);
 
     const uint32_t tid = threadIdx.x;
     const int c = a.c, w = a.w, h = a.h;
@@ -898,6 +906,36 @@ bool launch_if_shape(cudaStream_t st, void *psi, const TileArgs &a, const void *
     return true;
 }
 
+// Compiled shapes the ensemble kernel dispatches to (complex64, 12-bit tiles): the slot passes
+// of two bit groups, i.e. of the 12 lowest spins and of windows of 4, 6, 8 and 10 spins (the
+// systems of N = 16, 18, 20, 22 with 2 coalescing spins).  ens_shape: 1 + the index in this list.
+namespace ens {
+using Low12 = PassShape<1, Step<1, 0, 5, 0, 0, 0>, Step<0, 0, 5, 0, 0, 0>, Step<2, 3, 5, 1, 3, 5>,
+                        Step<0, 0, 0, 0, 0, 5>, Step<1, 0, 0, 0, 0, 5>>;
+using Win4 = PassShape<0, Step<0, 0, 4, 1, 0, 4>>;
+using Win6 = PassShape<0, Step<0, 0, 5, 0, 0, 0>, Step<1, 0, 1, 1, 0, 1>, Step<0, 0, 0, 0, 0, 5>>;
+using Win8 = PassShape<0, Step<0, 0, 5, 0, 0, 0>, Step<1, 0, 3, 1, 0, 3>, Step<0, 0, 0, 0, 0, 5>>;
+using Win10 = PassShape<0, Step<0, 0, 5, 0, 0, 0>, Step<1, 0, 5, 1, 0, 5>, Step<0, 0, 0, 0, 0, 5>>;
+} // namespace ens
+
+// Host: the ensemble shape of a complex64 12-bit pass (0 if none), N <= 32 and a slot required.
+inline int ensemble_shape_id(const TileArgs &a)
+{
+    if (!a.has_slot || a.ham.N > 32)
+        return 0;
+    if (ShapeOf<ens::Low12>::matches(a.io.chunk, a.nsteps, a.steps))
+        return 1;
+    if (ShapeOf<ens::Win4>::matches(a.io.chunk, a.nsteps, a.steps))
+        return 2;
+    if (ShapeOf<ens::Win6>::matches(a.io.chunk, a.nsteps, a.steps))
+        return 3;
+    if (ShapeOf<ens::Win8>::matches(a.io.chunk, a.nsteps, a.steps))
+        return 4;
+    if (ShapeOf<ens::Win10>::matches(a.io.chunk, a.nsteps, a.steps))
+        return 5;
+    return 0;
+}
+
 // Persistent ensemble kernel: every pass of every state of every system of a batch in one
 // launch (the typical-state ensembles of App. A).
 //
@@ -975,6 +1013,7 @@ k_tile_ensemble(const BatchSys *__restrict__ sys, const TileArgs *__restrict__ a
     __shared__ int w_go, w_pass, w_sys, w_ntiles;
     __shared__ uint32_t w_state;
     __shared__ uint64_t w_tile0;
+    __shared__ TileShared<R, TB, RB> sh_ens;   // slot state shared by the inlined pass builds
     const uint64_t total = sy.pstart[sy.npass];
     unsigned long long next = 0;   // thread 0: the ticket fetched ahead
     int pass_hint = 0;             // thread 0: tickets only grow, so the pass search starts here
@@ -1022,12 +1061,34 @@ k_tile_ensemble(const BatchSys *__restrict__ sys, const TileArgs *__restrict__ a
         const TileArgs &a = args[(size_t)p * nsys + s];
         const TileTab<R, TB, RB> *tabs = reinterpret_cast<const TileTab<R, TB, RB> *>(bs.tabs);
         // a pass without a slot (the middle passes of three or more bit groups) runs the code
-        // path compiled without the slot machinery, as ts_step's separate kernel build does
-        if (a.has_slot) {
+        // path compiled without the slot machinery, as ts_step's separate kernel build does;
+        // complex64 12-bit passes of a compiled shape run that build (ens_shape)
+        auto tiles = [&](auto shape_tag) {
+            using SH = typename decltype(shape_tag)::type;
+            for (int k = 0; k < nt; k++) {
+                if (k)
+                    __syncthreads();
+                tile_pass<R, TB, RB, true, true, SH, -1, 1, true>(psi, a, tabs, f0 + k, &sh_ens);
+            }
+        };
+        bool done_shape = false;
+        if constexpr (sizeof(R) == 4 && TB == 12 && RB == 5) {
+            done_shape = true;
+            switch (a.ens_shape) {
+            case 1: tiles(TypeTag<ens::Low12>{}); break;
+            case 2: tiles(TypeTag<ens::Win4>{}); break;
+            case 3: tiles(TypeTag<ens::Win6>{}); break;
+            case 4: tiles(TypeTag<ens::Win8>{}); break;
+            case 5: tiles(TypeTag<ens::Win10>{}); break;
+            default: done_shape = false; break;
+            }
+        }
+        if (done_shape) {
+        } else if (a.has_slot) {
             for (int k = 0; k < nt; k++) {
                 if (k)
                     __syncthreads();   // the previous tile's shared-memory reads are done
-                tile_pass<R, TB, RB, true, true>(psi, a, tabs, f0 + k);
+                tile_pass<R, TB, RB, true, true, RuntimeShape, -1, -1, true>(psi, a, tabs, f0 + k, &sh_ens);
             }
         } else {
             for (int k = 0; k < nt; k++) {
