@@ -466,6 +466,89 @@ template <int KIO_, typename... S> struct PassShape {
     static constexpr int KIO = KIO_;
     static constexpr int NS = (int)sizeof...(S);
     static constexpr int KPH = (0 + ... + (S::PH ? S::K : 0));   // chunk of the step with the slot
+    // the group's window size h: the highest local bit the steps rotate, plus one
+    template <int TB, int RB> static constexpr int h()
+    {
+        int m = 0;
+        ((m = (chunk_w<TB, RB>(S::K) + (S::R0HI > S::R1HI ? S::R0HI : S::R1HI)) > m
+                  ? chunk_w<TB, RB>(S::K) + (S::R0HI > S::R1HI ? S::R0HI : S::R1HI)
+                  : m),
+         ...);
+        return m;
+    }
+};
+
+// The I/O layout (thread bit -> local bit) of a tile whose group has h window spins, as the host
+// builds it (make_io in ts4_api.cu).  It depends on (h, TB, RB, ES) only: the TB - h lowest
+// spins always sort before the window spins, wherever the window sits.  Compiled shapes form the
+// thread's local base and global offset from it with a few bit operations instead of reading
+// the per-group table; the host launches them only when this layout equals the table's.
+template <int TB, int RB, int ES> struct StaticIO {
+    uint8_t bits[16];
+    __host__ __device__ constexpr StaticIO(int h, int io_chunk) : bits{}
+    {
+        const int W = io_chunk == 0 ? 0 : (RB < TB - RB ? RB : TB - RB);
+        int tb[32] = {};
+        int ntb = 0;
+        for (int l = h; l < TB; l++)      // the lowest spins (global positions 0 .. TB - h - 1)
+            if (l < W || l >= W + RB)
+                tb[ntb++] = l;
+        for (int l = 0; l < h; l++)       // then the window spins
+            if (l < W || l >= W + RB)
+                tb[ntb++] = l;
+        int set[5] = {}, lanes[32] = {};
+        bool in_set[32] = {}, in_lanes[32] = {};
+        int ns = 0, seen = 0;
+        for (int i = 0; i < ntb && ns < 5; i++)
+            if (tb[i] >= h) {
+                set[ns++] = tb[i];
+                in_set[tb[i]] = true;
+                seen |= contrib(tb[i]);
+            }
+        for (int i = 0; i < ntb; i++)
+            if (ns < 5 && !in_set[tb[i]] && contrib(tb[i]) && !(seen & contrib(tb[i]))) {
+                set[ns++] = tb[i];
+                in_set[tb[i]] = true;
+                seen |= contrib(tb[i]);
+            }
+        for (int i = 0; i < ntb; i++)
+            if (ns < 5 && !in_set[tb[i]]) {
+                set[ns++] = tb[i];
+                in_set[tb[i]] = true;
+            }
+        const int need = ES == 8 ? 4 : 3;
+        int n = 0, got = 0;
+        for (int i = 0; i < ns; i++)
+            if (n < need && contrib(set[i]) && !(got & contrib(set[i]))) {
+                lanes[n++] = set[i];
+                in_lanes[set[i]] = true;
+                got |= contrib(set[i]);
+            }
+        for (int i = 0; i < ns; i++)
+            if (!in_lanes[set[i]]) {
+                lanes[n++] = set[i];
+                in_lanes[set[i]] = true;
+            }
+        for (int l = 0; l < TB; l++)
+            if ((l < W || l >= W + RB) && !in_lanes[l])
+                lanes[n++] = l;
+        for (int i = 0; i < n && i < 16; i++)
+            bits[i] = (uint8_t)lanes[i];
+    }
+    static __host__ __device__ constexpr int contrib(int k)
+    {
+        const uint32_t e = 1u << k;
+        const uint32_t p = ES == 8 ? e + (e >> 5) + (e >> 10) : e + (e >> 4) + (e >> 8);
+        return (int)(p & (ES == 8 ? 15u : 7u));
+    }
+    // host check against the layout the schedule built
+    bool equals(const uint8_t *b) const
+    {
+        for (int t = 0; t < TB - RB; t++)
+            if (bits[t] != b[t])
+                return false;
+        return true;
+    }
 };
 struct RuntimeShape {};
 template <typename T> struct TypeTag {
@@ -610,22 +693,28 @@ template <typename R, int TB, int RB> struct TileKernel {
             apply_slot(x, sh, mode);
     }
 
-    // the steps of a compile-time shape (see PassShape), from layout CUR; back to KIO at the end
-    template <int CUR, int KIO, bool SLOT, int MODE, typename BaseOf, typename SH>
+    // the steps of a compile-time shape (see PassShape), from layout CUR; back to KIO at the end.
+    // FIRST: no transpose yet in this pass.  The transpose buffer has then been untouched since
+    // the barrier that ends the pass's prologue (and, in a persistent kernel, since the barrier
+    // between tiles), so the first transpose needs no barrier before its stores.
+    template <int CUR, int KIO, bool SLOT, int MODE, bool FIRST, typename BaseOf, typename SH>
     static __device__ __forceinline__ void run_shape(C (&x)[NR], C *sm, const BaseOf &base_of, const SH &sh, int mode)
     {
         if constexpr (CUR != KIO) {
-            __syncthreads();
+            if constexpr (!FIRST)
+                __syncthreads();
             store_chunk<CUR>(sm, padidx<ES>(base_of(CUR)), x);
             __syncthreads();
             load_chunk<KIO>(sm, padidx<ES>(base_of(KIO)), x);
         }
     }
-    template <int CUR, int KIO, bool SLOT, int MODE, typename BaseOf, typename SH, typename S0, typename... Rest>
+    template <int CUR, int KIO, bool SLOT, int MODE, bool FIRST, typename BaseOf, typename SH, typename S0,
+              typename... Rest>
     static __device__ __forceinline__ void run_shape(C (&x)[NR], C *sm, const BaseOf &base_of, const SH &sh, int mode)
     {
         if constexpr (S0::K != CUR) {
-            __syncthreads();
+            if constexpr (!FIRST)
+                __syncthreads();
             store_chunk<CUR>(sm, padidx<ES>(base_of(CUR)), x);
             __syncthreads();
             load_chunk<S0::K>(sm, padidx<ES>(base_of(S0::K)), x);
@@ -634,13 +723,13 @@ template <typename R, int TB, int RB> struct TileKernel {
         if constexpr (SLOT && S0::PH)
             apply_slot_m<MODE>(x, sh, mode);
         wht_fixed<S0::R1LO, S0::R1HI>(x);
-        run_shape<S0::K, KIO, SLOT, MODE, BaseOf, SH, Rest...>(x, sm, base_of, sh, mode);
+        run_shape<S0::K, KIO, SLOT, MODE, FIRST && (S0::K == CUR), BaseOf, SH, Rest...>(x, sm, base_of, sh, mode);
     }
     template <bool SLOT, int MODE, typename BaseOf, typename SH, int KIO, typename... S>
     static __device__ __forceinline__ void run_pass_shape(C (&x)[NR], C *sm, const BaseOf &base_of, const SH &sh,
                                                           int mode, PassShape<KIO, S...>)
     {
-        run_shape<KIO, KIO, SLOT, MODE, BaseOf, SH, S...>(x, sm, base_of, sh, mode);
+        run_shape<KIO, KIO, SLOT, MODE, true, BaseOf, SH, S...>(x, sm, base_of, sh, mode);
     }
 };
 
@@ -712,9 +801,25 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
 
     // ---- I/O layout: this thread's local base and global offset (host table) and the
     // global offsets of the register bits
-    const uint4 iom = a.iomap[tid];
-    const uint32_t base_io = iom.z;
-    uint64_t gthr = gbase | ((uint64_t)iom.y << 32 | iom.x);
+    uint32_t base_io;
+    uint64_t gthr;
+    if constexpr (!ST::runtime) {
+        // compiled shape: the I/O layout is known at compile time (StaticIO); the local base is
+        // a scatter of the thread index, its global offset the window bits shifted to w and the
+        // lowest spins below them
+        constexpr int H = SHAPE::template h<TB, RB>();
+        constexpr StaticIO<TB, RB, ES> sio(H, SHAPE::KIO);
+        uint32_t bl = 0;
+#pragma unroll
+        for (int t = 0; t < K::NTB; t++)
+            bl |= ((tid >> t) & 1u) << sio.bits[t];
+        base_io = bl;
+        gthr = gbase | ((uint64_t)(bl & ((1u << H) - 1u)) << w) | (uint64_t)(bl >> H);
+    } else {
+        const uint4 iom = a.iomap[tid];
+        base_io = iom.z;
+        gthr = gbase | ((uint64_t)iom.y << 32 | iom.x);
+    }
     uint64_t gst[RB];
 #pragma unroll
     for (int b = 0; b < RB; b++)
@@ -883,6 +988,18 @@ bool launch_shaped(cudaStream_t st, void *psi, const TileArgs &a, const void *ta
 template <> bool launch_shaped<float, 12, 5>(cudaStream_t, void *, const TileArgs &, const void *, uint64_t, cudaError_t *);
 template <> bool launch_shaped<double, 12, 4>(cudaStream_t, void *, const TileArgs &, const void *, uint64_t, cudaError_t *);
 
+// Host: the pass's group has the window size of SHAPE and the I/O layout StaticIO gives it, so the
+// compiled build may form its I/O addresses without the table.
+template <typename R, int TB, int RB, typename SHAPE> bool shape_io_ok(const TileArgs &a)
+{
+    constexpr int H = SHAPE::template h<TB, RB>();
+    constexpr int ES = (int)sizeof(typename CT<R>::T);
+    if (a.h != H || a.c != TB - H)
+        return false;
+    const StaticIO<TB, RB, ES> sio(H, SHAPE::KIO);
+    return sio.equals(a.io.bits);
+}
+
 // One compiled shape: launches k_tile<..., SHAPE, MODE, NARROW> if the pass has that shape, that
 // slot-factor form (MODE, slot passes of complex64 only; -1 = any) and that offset width
 // (NARROW: 1 for N <= 32, 0 above).
@@ -892,6 +1009,8 @@ bool launch_if_shape(cudaStream_t st, void *psi, const TileArgs &a, const void *
     if ((a.has_slot != 0) != SLOT || !ShapeOf<SHAPE>::matches(a.io.chunk, a.nsteps, a.steps))
         return false;
     if ((MODE >= 0 && a.exact_sincos != MODE) || ((a.ham.N <= 32) != (NARROW != 0)))
+        return false;
+    if (!shape_io_ok<R, TB, RB, SHAPE>(a))
         return false;
     using K = TileKernel<R, TB, RB>;
     constexpr size_t smem = sizeof(typename CT<R>::T) * K::SMEM_ELEMS;
@@ -923,15 +1042,19 @@ inline int ensemble_shape_id(const TileArgs &a)
 {
     if (!a.has_slot || a.ham.N > 32)
         return 0;
-    if (ShapeOf<ens::Low12>::matches(a.io.chunk, a.nsteps, a.steps))
+    auto ok = [&](auto tag) {
+        using SH = typename decltype(tag)::type;
+        return ShapeOf<SH>::matches(a.io.chunk, a.nsteps, a.steps) && shape_io_ok<float, 12, 5, SH>(a);
+    };
+    if (ok(TypeTag<ens::Low12>{}))
         return 1;
-    if (ShapeOf<ens::Win4>::matches(a.io.chunk, a.nsteps, a.steps))
+    if (ok(TypeTag<ens::Win4>{}))
         return 2;
-    if (ShapeOf<ens::Win6>::matches(a.io.chunk, a.nsteps, a.steps))
+    if (ok(TypeTag<ens::Win6>{}))
         return 3;
-    if (ShapeOf<ens::Win8>::matches(a.io.chunk, a.nsteps, a.steps))
+    if (ok(TypeTag<ens::Win8>{}))
         return 4;
-    if (ShapeOf<ens::Win10>::matches(a.io.chunk, a.nsteps, a.steps))
+    if (ok(TypeTag<ens::Win10>{}))
         return 5;
     return 0;
 }
