@@ -6,7 +6,7 @@
 //   slot passes (rotate the group, slot, rotate again) of window groups of 4..10 spins (their
 //   tiles keep the lowest spins) and of the group of the 12 lowest spins (two bit groups);
 //   passes without a slot of the 12 lowest spins (the middle of three bit groups) and of
-//   windows of 7 and 8 spins (four bit groups, N = 31..34).
+//   windows of 7 and 8 spins (four bit groups, N = 33, 34).
 // The slot-factor form of the usual small angles and the 32-bit element offsets of N <= 32 are
 // compiled in as well (MODE, NARROW of k_tile); passes with other values take the builds that
 // read them at run time.
@@ -53,7 +53,12 @@ bool launch_shaped<float, 12, 5>(cudaStream_t st, void *psi, const TileArgs &a, 
            launch_if_shape<R, 12, 5, true, SlotWin10>(st, psi, a, tabs, nblk, err) ||
            launch_if_shape<R, 12, 5, true, SlotWin4>(st, psi, a, tabs, nblk, err) ||
            launch_if_shape<R, 12, 5, true, SlotLow12>(st, psi, a, tabs, nblk, err) ||
-           // four bit groups (N = 31..34): window passes without a slot, 32- or 64-bit offsets
+           // N = 33, 34 (64-bit offsets): the slot passes of their 7- and 8-spin windows
+           launch_if_shape<R, 12, 5, true, SlotWin7, 0, 0>(st, psi, a, tabs, nblk, err) ||
+           launch_if_shape<R, 12, 5, true, SlotWin8, 0, 0>(st, psi, a, tabs, nblk, err) ||
+           launch_if_shape<R, 12, 5, true, SlotWin7, -1, 0>(st, psi, a, tabs, nblk, err) ||
+           launch_if_shape<R, 12, 5, true, SlotWin8, -1, 0>(st, psi, a, tabs, nblk, err) ||
+           // four bit groups (N = 33, 34): window passes without a slot, 32- or 64-bit offsets
            launch_if_shape<R, 12, 5, false, RotWin7, -1, 1>(st, psi, a, tabs, nblk, err) ||
            launch_if_shape<R, 12, 5, false, RotWin8, -1, 1>(st, psi, a, tabs, nblk, err) ||
            launch_if_shape<R, 12, 5, false, RotWin7, -1, 0>(st, psi, a, tabs, nblk, err) ||
