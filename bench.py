@@ -606,6 +606,68 @@ def run_phase_table_ab(args):
                       "tables": "complex64: 3 x 2^N floats; complex128: 3 x 2^N doubles"}), flush=True)
 
 
+def run_pass_times(args):
+    """Time per amplitude and pass with the state in L2 (N <= 23: at most 64 MB) and in HBM (N >= 25),
+    complex64 dipolar chain, default schedule: the whole step with CUDA events, and each kind of
+    k_tile launch from CUPTI activity records (torch.profiler; kernels back to back on one stream,
+    no cache flush between them).  Kinds: slot passes and passes without a slot of compiled
+    shapes, and the builds that follow the step list at run time (first and last pass of a call).
+    One JSON line."""
+    import numpy as np
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+    from paper_1305_0036_gb300 import build
+    build.build()
+    from paper_1305_0036_gb300 import ts4, workloads as W
+    torch.cuda.set_device(0)
+    # the first profiling session of a process can come back without kernel records: open one
+    # on a throwaway launch first
+    with profile(activities=[ProfilerActivity.CUDA]):
+        torch.ones(1024, device="cuda").mul_(2.0)
+        torch.cuda.synchronize()
+    rows = []
+    for N in args.pt_sizes:
+        ctx = ts4.Context.from_system(W.dipolar_chain(N), prec="c64")
+        ctx.set_state(W.random_phase_state(N, W.SEED_BASE + 3, np.complex64))
+        sch = ctx.schedule()
+        ctx.step(TAU, 2)
+        torch.cuda.synchronize()
+        n = 40 if N < 26 else 10
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(ctx.stream)
+        ctx.step(TAU, n)
+        b.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / n
+        row = {"N": N, "state_mb": 2 ** N * 8 / 1e6, "groups": sch["groups"],
+               "passes_per_step": sch["passes_per_step"], "ms_per_step": ms,
+               "ps_per_amp_pass": ms * 1e9 / 2 ** N / sch["passes_per_step"]}
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            ctx.step(TAU, 4)
+            torch.cuda.synchronize()
+        kinds = {}
+        for ev in prof.events():
+            if ev.device_type != torch.autograd.DeviceType.CUDA or "k_tile<" not in ev.name:
+                continue
+            if "PassShape" not in ev.name:
+                kind = "run-time build"
+            elif "k_tile<float, 12, 5, true" in ev.name:
+                kind = "slot pass"
+            else:
+                kind = "pass without slot"
+            t = ev.device_time if hasattr(ev, "device_time") else ev.cuda_time
+            k = kinds.setdefault(kind, [0, 0.0])
+            k[0] += 1
+            k[1] += t
+        row["kernels"] = {k: {"launches": v[0], "mean_us": v[1] / v[0], "ps_per_amp": v[1] / v[0] * 1e6 / 2 ** N}
+                          for k, v in sorted(kinds.items())}
+        rows.append(row)
+        ctx.close()
+        torch.cuda.empty_cache()
+    print(json.dumps({"pass_times": rows, "workload": "dipolar XXZ chain, random-phase state, tau=0.01, complex64",
+                      "l2_mb": 129}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -626,12 +688,18 @@ def main():
                     help="time the paper's phase-table mode against bit tests and the fused pass instead")
     ap.add_argument("--ab-sizes", type=int, nargs="+", default=[22, 26, 28])
     ap.add_argument("--ab-steps", type=int, default=1)
+    ap.add_argument("--pass-times", action="store_true",
+                    help="time each kind of pass per amplitude at the sizes in --pt-sizes instead")
+    ap.add_argument("--pt-sizes", type=int, nargs="+", default=[22, 23, 24, 25, 26, 28])
     ap.add_argument("--spins", type=int, default=28,
                     help="chain length N (28 is the benchmark; smaller N only for profiling captures)")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.phase_table_ab:
         run_phase_table_ab(args)
+        return
+    if args.pass_times:
+        run_pass_times(args)
         return
     if args.impl == "reference":
         run_reference(args, ws, rank)
