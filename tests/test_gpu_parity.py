@@ -8,6 +8,8 @@ Tolerances
               multiplications, all of relative size u; the bound is their worst-case
               linear accumulation for a unit-norm state.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -78,6 +80,100 @@ def test_fused_c64_matches_oracle(ts4, N, tb64, tb128, cb):
     assert sched["kernel"] == ts4.TS_KERNEL_FUSED and sched["tile_bits"] == min(tb64, N)
     err = np.linalg.norm(got - ref)
     assert err <= _c64_bound(N, 20 * nsteps), err
+
+
+MANY_GROUPS = [
+    # (precision, N, tile bits, coalescing bits, groups): groups of 12 + 4 + 4 + 3,
+    # 11 + 4 + 3 + 3 and 11 + 4 + 3 + 3 + 3 spins; the groups between the slot-carrying ones
+    # are rotated by passes without a slot
+    ("c64", 23, 12, 7, 4),
+    ("c128", 21, 11, 7, 4),
+    ("c128", 24, 11, 7, 5),
+]
+
+
+@functools.lru_cache(maxsize=None)
+def _many_groups_case(prec, N):
+    """System, initial state (as the run holds it) and two oracle TS4 steps, tau = 0.05."""
+    s = W.random_system(N, 700 + N, transverse=True)
+    psi0 = W.haar_state(N, 750 + N)
+    if prec == "c64":
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)   # what the run starts from
+    return s, psi0, oracle.ts4(psi0, _ham(s), 0.05, 2)
+
+
+@pytest.mark.parametrize("prec,N,tb,cb,ng", MANY_GROUPS)
+@pytest.mark.parametrize("chained", [False, True])
+def test_four_and_five_bit_groups_match_oracle(ts4, prec, N, tb, cb, ng, chained):
+    """The zigzag over four or five bit groups (four is the schedule of N=33 and N=34, where the
+    oracle cannot run) at sizes the oracle finishes in seconds: two TS4 steps in one call, or
+    as chained one-step calls.  complex128 within 1e-12 of the oracle; complex64 within the L2
+    bound and, per amplitude, within the Gaussian-tail multiple of it used for the benchmark's
+    schedules (c = sqrt(2 ln 2^(N+1)) times the bound times max|psi|)."""
+    s, psi0, ref = _many_groups_case(prec, N)
+    nsteps, tau = 2, 0.05
+    ctx = ts4.Context.from_system(s, prec=prec)
+    ctx.set_schedule(ts4.TS_KERNEL_FUSED, tb, cb)
+    sch = ctx.schedule()
+    assert (sch["groups"], sch["tile_bits"]) == (ng, tb)
+    ctx.set_state(psi0.astype(np.complex64) if prec == "c64" else psi0)
+    if chained:
+        ctx.set_chaining(True)
+        for _ in range(nsteps):
+            ctx.step(tau, 1)
+    else:
+        ctx.step(tau, nsteps)
+    got = ctx.get_state().astype(np.complex128)
+    ctx.close()
+    err = got - ref
+    el, l2 = np.abs(err).max(), np.linalg.norm(err)
+    if prec == "c128":
+        print(f"\nc128 N={N}, {ng} groups, chained={chained}: max|dpsi| = {el:.3e} (bound 1e-12)")
+        assert el <= 1e-12, el
+    else:
+        bound = _c64_bound(N, 20 * nsteps + 1)
+        el_bound = np.sqrt(2.0 * np.log(2.0 ** (N + 1))) * bound * np.abs(ref).max()
+        print(f"\nc64 N={N}, {ng} groups, chained={chained}: ||dpsi||_2 = {l2:.3e} (bound {bound:.3e}), "
+              f"max|dpsi| = {el:.3e} (bound {el_bound:.3e})")
+        assert l2 <= bound, l2
+        assert el <= el_bound, el
+
+
+def test_four_groups_with_seven_spin_windows_n32_c64(ts4):
+    """N=32 complex64 (34 GB) with 3 coalescing spins: groups of 12 + 7 + 7 + 6 spins, so the
+    7-spin window group is rotated by passes without a slot (the compiled window shape of N=33
+    with 32-bit offsets).  One TS4 step of the XYZ chain from the Neel state against the default
+    schedule (12 + 10 + 10 spins, three groups: the geometry checked against the oracle at
+    N=27 and N=28), both compared on the device: the two runs share no window pass, and each
+    is within the c64 L2 bound of the exact step, so they differ by at most twice that."""
+    import torch
+    torch.cuda.empty_cache()
+    N = 32
+    s = W.xyz_chain(N, 1.0, 0.8, 0.5, h=0.1)
+    neel = W.neel_index(N)
+    runs = []
+    for cb in (3, 0):
+        ctx = ts4.Context.from_system(s, prec="c64")
+        ctx.set_schedule(ts4.TS_KERNEL_FUSED, 12, cb)
+        runs.append((ctx, ctx.schedule()))
+        ctx.set_basis_state(neel)
+        ctx.step(0.02, 1)
+    (a, sa), (b, sb) = runs
+    assert (sa["groups"], sb["groups"]) == (4, 3)
+    d2, dmax = 0.0, 0.0
+    chunk = 1 << 28
+    for i in range(0, 1 << N, chunk):
+        d = (a.psi[i:i + chunk] - b.psi[i:i + chunk]).abs()
+        d2 += float((d.double() ** 2).sum())
+        dmax = max(dmax, float(d.max()))
+    bound = 2 * _c64_bound(N, 21)
+    print(f"\nc64 N=32, 4 groups vs 3 groups: ||dpsi||_2 = {d2 ** 0.5:.3e}, max|dpsi| = {dmax:.3e} "
+          f"(bound {bound:.3e})")
+    assert d2 ** 0.5 <= bound
+    assert abs(a.norm() - 1.0) <= 1e-5 and abs(b.norm() - 1.0) <= 1e-5
+    a.close()
+    b.close()
+    torch.cuda.empty_cache()
 
 
 def test_hundred_steps_multi_group_matches_oracle(ts4):

@@ -60,8 +60,8 @@ def replay(groups, passes, layers, state=None, slot_base=0, complete=True):
 
 
 @pytest.mark.parametrize("N,tb,cb", [(12, 12, 3), (14, 12, 2), (17, 12, 3), (20, 12, 3), (23, 12, 2),
-                                     (25, 12, 3), (28, 12, 3), (28, 13, 3), (28, 14, 4), (33, 12, 3),
-                                     (34, 12, 3)])
+                                     (23, 12, 7), (25, 12, 3), (28, 12, 3), (28, 12, 7), (28, 13, 3),
+                                     (28, 14, 4), (32, 12, 3), (33, 12, 3), (34, 12, 3)])
 @pytest.mark.parametrize("order", [4, 2, 1])
 def test_plan_replays_to_the_full_decomposition(ts4, N, tb, cb, order):
     nsteps = 2
@@ -123,7 +123,7 @@ def test_plan_rejects_bad_arguments(ts4):
             ts4.ts_plan(*args)
 
 
-@pytest.mark.parametrize("N,tb,cb", [(17, 12, 3), (23, 12, 2), (28, 12, 3), (33, 12, 3)])
+@pytest.mark.parametrize("N,tb,cb", [(17, 12, 3), (23, 12, 2), (23, 12, 7), (28, 12, 3), (28, 12, 7), (33, 12, 3)])
 @pytest.mark.parametrize("order", [4, 2])
 def test_chained_calls_replay_as_one_run(ts4, N, tb, cb, order):
     """Calls with chaining (ts_set_chaining): the first holds back its final pass, the middle
